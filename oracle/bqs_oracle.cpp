@@ -1,0 +1,459 @@
+// BlockQuicksort CPU oracle -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.
+//
+// A plain, slow, single-threaded restatement of BlockQuicksort (Edelkamp & Weiss,
+// "BlockQuicksort: How Branch Mispredictions don't affect Quicksort", arXiv 1604.06697).
+// It exists only to check the CUDA path: only tests/, __graft_entry__.smoke() and the
+// cpu_baseline / reference leg of bench.py may load it.  It shares no code, header,
+// table or helper with the CUDA library, and the CUDA library never calls it.
+//
+// What it computes, part by part (all citations are to the paper):
+//   * Quicksort main loop (Sec. 2 "Quicksort and improvements", Algorithm 1, and the
+//     main loop of Appendix B): explicit stack, the larger side is stacked and the loop
+//     continues on the smaller side; the pivot is excluded from both sides; Introsort
+//     depth limit 2*floor(log2 n)+3 with Heapsort for an over-deep sub-array;
+//     Insertionsort for sub-arrays of at most 16 elements.
+//   * Pivot selection (Sec. 2 and Sec. 4 "Different Pivot Selection Methods"):
+//     median-of-three of (first, middle, last), and median of a sqrt(n) sample which
+//     falls back to median-of-five-medians-of-five below 20000 elements and to
+//     median-of-three for small arrays.
+//   * Block partitioning (Sec. 3, Algorithm 3) with B = 128, including the final scan
+//     of the at most 2B remaining elements and the compaction of the one buffer that may
+//     still hold misplaced elements (Sec. 3, the "basic variant" of Appendix B).
+//   * The plain definition of a value partition (Sec. 2 "Quicksort and improvements":
+//     smaller-or-equal left, greater-or-equal right), in its stable "count(<pivot)" form.
+//
+// Readings where the paper is silent or garbled:
+//   * Algorithm 3's scanning comparisons are printed with the directions swapped; the
+//     prose of Sec. 3 fixes them: the left buffer collects elements >= pivot, the right
+//     buffer elements <= pivot.
+//   * The median-of-three sample is (first, first + floor(len/2), last).
+//   * sqrt(n) sample: k = floor(sqrt(len)) | 1 equally spaced positions
+//     b + floor((2i+1) len / (2k)); the pivot is the sample's median (rank (k-1)/2).
+//     Median-of-three is used below 64 elements.
+//   * float64 is ordered by the total order ord(x) = bits(x) ^ (sign ? ~0 : 1<<63),
+//     which equals IEEE "<" on non-NaN values except that -0.0 < +0.0.
+//   * Key-value pairs are ordered lexicographically by (key, payload).
+//
+// Build: g++ -O2 -std=c++17 -shared -fPIC bqs_oracle.cpp -o liboracle_bqs.so
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+namespace {
+
+// Block size B: Sec. 3 fixes it at 128 elements for all experiments.
+constexpr int64_t kB = 128;
+
+struct Counters {
+  uint64_t comparisons = 0;      // every call of the order predicate
+  uint64_t partitions = 0;       // calls of the block partitioner from the main loop
+  uint64_t insertion_sorts = 0;  // recursion stoppers: Insertionsort
+  uint64_t heap_sorts = 0;       // recursion stoppers: Heapsort (depth limit exceeded)
+  uint64_t depth_limit = 0;      // the Introsort limit the main loop used
+  uint64_t max_depth = 0;        // deepest level at which a partition ran (root = 1)
+};
+
+enum PivotRule { kMedianOf3 = 0, kMedianOfSqrt = 1 };
+
+// ---- element types and their strict weak orders ---------------------------------
+
+uint64_t ord_f64(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, sizeof u);
+  return (u >> 63) ? ~u : (u | (uint64_t(1) << 63));
+}
+
+struct LessI32 { bool operator()(int32_t a, int32_t b) const { return a < b; } };
+struct LessI64 { bool operator()(int64_t a, int64_t b) const { return a < b; } };
+struct LessF64 { bool operator()(double a, double b) const { return ord_f64(a) < ord_f64(b); } };
+
+template <class K>
+struct Pair { K key; uint32_t val; };
+
+template <class K, class KeyLess>
+struct LessPair {
+  bool operator()(const Pair<K>& a, const Pair<K>& b) const {
+    KeyLess kl;
+    if (kl(a.key, b.key)) return true;
+    if (kl(b.key, a.key)) return false;
+    return a.val < b.val;
+  }
+};
+
+int64_t floor_log2(int64_t n) {  // floor(log2 n) for n >= 1, the paper's ilogb(n)
+  int64_t r = 0;
+  while (n > 1) { n >>= 1; ++r; }
+  return r;
+}
+
+int64_t isqrt(int64_t n) {
+  int64_t r = (int64_t)std::sqrt((double)n);
+  while (r * r > n) --r;
+  while ((r + 1) * (r + 1) <= n) ++r;
+  return r;
+}
+
+template <class T, class Less>
+struct Sorter {
+  Counters& cnt;
+  int pivot_rule;
+  int64_t is_thresh;     // Insertionsort for sub-arrays of at most this many elements
+  int64_t depth_limit;   // < 0: 2*floor(log2 n)+3
+
+  bool lt(const T& a, const T& b) {
+    ++cnt.comparisons;
+    return Less()(a, b);
+  }
+
+  // ---- recursion stoppers ---------------------------------------------------------
+
+  // Insertionsort (textbook, Knuth 5.2.1) on A[b, e).
+  void insertion_sort(T* A, int64_t b, int64_t e) {
+    ++cnt.insertion_sorts;
+    for (int64_t i = b + 1; i < e; ++i) {
+      T x = A[i];
+      int64_t j = i;
+      while (j > b && lt(x, A[j - 1])) {
+        A[j] = A[j - 1];
+        --j;
+      }
+      A[j] = x;
+    }
+  }
+
+  // Heapsort (Williams 1964, with Floyd's bottom-up heap construction) on A[b, e).
+  void sift_down(T* H, int64_t root, int64_t n) {
+    for (;;) {
+      int64_t child = 2 * root + 1;
+      if (child >= n) return;
+      if (child + 1 < n && lt(H[child], H[child + 1])) ++child;
+      if (!lt(H[root], H[child])) return;
+      std::swap(H[root], H[child]);
+      root = child;
+    }
+  }
+  void heap_sort(T* A, int64_t b, int64_t e) {
+    ++cnt.heap_sorts;
+    T* H = A + b;
+    int64_t n = e - b;
+    for (int64_t i = n / 2 - 1; i >= 0; --i) sift_down(H, i, n);
+    for (int64_t m = n - 1; m > 0; --m) {
+      std::swap(H[0], H[m]);
+      sift_down(H, 0, m);
+    }
+  }
+
+  // ---- pivot selection ------------------------------------------------------------
+
+  // Conditional exchange leaving A[i] <= A[j] (the "sort_pair" step of Appendix B).
+  void order2(T* A, int64_t i, int64_t j) {
+    if (lt(A[j], A[i])) std::swap(A[i], A[j]);
+  }
+
+  // Median of three positions: the three values are put into order in place and the
+  // position of the middle one is returned.  Afterwards A[i] <= pivot <= A[k].
+  int64_t median_of_3(T* A, int64_t i, int64_t j, int64_t k) {
+    order2(A, i, j);
+    order2(A, j, k);
+    order2(A, i, j);
+    return j;
+  }
+
+  // Position of the median (rank (m-1)/2) of the values at the positions pos[0, m).
+  // The selection step is the library's std::nth_element (the paper does the same).
+  int64_t median_position(T* A, std::vector<int64_t> pos) {
+    size_t mid = (pos.size() - 1) / 2;
+    std::nth_element(pos.begin(), pos.begin() + mid, pos.end(),
+                     [&](int64_t x, int64_t y) { return lt(A[x], A[y]); });
+    return pos[mid];
+  }
+
+  // Equally spaced sample of k positions of A[b, b+len): b + floor((2i+1) len / (2k)).
+  static std::vector<int64_t> spaced(int64_t b, int64_t len, int64_t k) {
+    std::vector<int64_t> p(k);
+    for (int64_t i = 0; i < k; ++i) p[i] = b + ((2 * i + 1) * len) / (2 * k);
+    return p;
+  }
+
+  // Median of five medians of five (Sec. 4): 25 equally spaced positions in five
+  // consecutive groups of five; the median of each group, then the median of those.
+  int64_t median_of_5_medians_of_5(T* A, int64_t b, int64_t len) {
+    std::vector<int64_t> p = spaced(b, len, 25), medians;
+    for (int g = 0; g < 5; ++g)
+      medians.push_back(median_position(A, std::vector<int64_t>(p.begin() + 5 * g, p.begin() + 5 * g + 5)));
+    return median_position(A, medians);
+  }
+
+  // ---- block partitioning (Algorithm 3) -------------------------------------------
+
+  // Partitions A[lo, hi) around the element at position piv.  Returns the pivot's
+  // final position p: A[lo, p) <= A[p] <= A(p, hi).
+  int64_t block_partition(T* A, int64_t lo, int64_t hi, int64_t piv) {
+    // The pivot is parked at the last position and left out of the scans.
+    std::swap(A[piv], A[hi - 1]);
+    piv = hi - 1;
+    const T pivot = A[piv];
+
+    int64_t l = lo;       // first element of the not yet partitioned window
+    int64_t r = hi - 2;   // last element of that window (inclusive)
+    int64_t offL[kB], offR[kB];  // offsets of misplaced elements in the current blocks
+    int64_t numL = 0, numR = 0, startL = 0, startR = 0;
+
+    // Main loop: while more than two blocks remain, refill whichever buffer is empty by
+    // scanning a whole block, then swap as many misplaced pairs as both buffers allow.
+    while (r - l + 1 > 2 * kB) {
+      if (numL == 0) {
+        startL = 0;
+        for (int64_t i = 0; i < kB; ++i) {   // left block: collect elements >= pivot
+          offL[numL] = i;
+          numL += !lt(A[l + i], pivot);
+        }
+      }
+      if (numR == 0) {
+        startR = 0;
+        for (int64_t i = 0; i < kB; ++i) {   // right block: collect elements <= pivot
+          offR[numR] = i;
+          numR += !lt(pivot, A[r - i]);
+        }
+      }
+      int64_t m = std::min(numL, numR);
+      for (int64_t j = 0; j < m; ++j) std::swap(A[l + offL[startL + j]], A[r - offR[startR + j]]);
+      numL -= m; numR -= m;
+      startL += m; startR += m;
+      if (numL == 0) l += kB;   // left block done
+      if (numR == 0) r -= kB;   // right block done
+    }
+
+    // Final scan: the window holds at most 2B elements.  An empty buffer's side is
+    // scanned as a (shorter) block that together with a pending block covers the window.
+    int64_t rest = r - l + 1, shiftL, shiftR;
+    if (numL == 0 && numR == 0) {
+      shiftL = rest / 2;
+      shiftR = rest - shiftL;
+      startL = startR = 0;
+      for (int64_t i = 0; i < shiftL; ++i) { offL[numL] = i; numL += !lt(A[l + i], pivot); }
+      for (int64_t i = 0; i < shiftR; ++i) { offR[numR] = i; numR += !lt(pivot, A[r - i]); }
+    } else if (numR != 0) {      // right block pending: scan the rest on the left
+      shiftL = rest - kB;
+      shiftR = kB;
+      startL = 0;
+      for (int64_t i = 0; i < shiftL; ++i) { offL[numL] = i; numL += !lt(A[l + i], pivot); }
+    } else {                     // left block pending: scan the rest on the right
+      shiftL = kB;
+      shiftR = rest - kB;
+      startR = 0;
+      for (int64_t i = 0; i < shiftR; ++i) { offR[numR] = i; numR += !lt(pivot, A[r - i]); }
+    }
+    int64_t m = std::min(numL, numR);
+    for (int64_t j = 0; j < m; ++j) std::swap(A[l + offL[startL + j]], A[r - offR[startR + j]]);
+    numL -= m; numR -= m;
+    startL += m; startR += m;
+    if (numL == 0) l += shiftL;
+    if (numR == 0) r -= shiftR;
+
+    // At most one buffer still holds misplaced elements; the window [l, r] is then
+    // exactly that buffer's block.  Move them to the far end of the block (no more
+    // comparisons), then swap the pivot into the gap.
+    if (numL != 0) {
+      // Elements >= pivot at l + offL[...] go to the right end of [l, r].
+      int64_t upper = r;
+      int64_t k = startL + numL - 1;
+      while (k >= startL && l + offL[k] == upper) { --upper; --k; }   // already in place
+      for (; k >= startL; --k, --upper) std::swap(A[upper], A[l + offL[k]]);
+      std::swap(A[piv], A[upper + 1]);
+      return upper + 1;
+    }
+    if (numR != 0) {
+      // Elements <= pivot at r - offR[...] go to the left end of [l, r].
+      int64_t lower = l;
+      int64_t k = startR + numR - 1;
+      while (k >= startR && r - offR[k] == lower) { ++lower; --k; }   // already in place
+      for (; k >= startR; --k, ++lower) std::swap(A[lower], A[r - offR[k]]);
+      std::swap(A[piv], A[lower]);
+      return lower;
+    }
+    std::swap(A[piv], A[l]);
+    return l;
+  }
+
+  // Chooses a pivot for A[b, e) and partitions; returns the pivot's final position.
+  int64_t partition(T* A, int64_t b, int64_t e) {
+    ++cnt.partitions;
+    int64_t len = e - b;
+    if (pivot_rule == kMedianOf3 || len < 64) {
+      // The sample's minimum and maximum end up at b and e-1, on their correct sides,
+      // so only A[b+1, e-1) is partitioned.
+      int64_t mid = median_of_3(A, b, b + len / 2, e - 1);
+      return block_partition(A, b + 1, e - 1, mid);
+    }
+    int64_t piv = (len < 20000) ? median_of_5_medians_of_5(A, b, len)
+                                : median_position(A, spaced(b, len, isqrt(len) | 1));
+    return block_partition(A, b, e, piv);
+  }
+
+  // ---- Quicksort main loop --------------------------------------------------------
+
+  void sort(T* A, int64_t n) {
+    if (n < 2) return;
+    const int64_t limit = depth_limit >= 0 ? depth_limit : 2 * floor_log2(n) + 3;
+    cnt.depth_limit = (uint64_t)limit;
+    struct Frame { int64_t b, e, depth; };
+    std::vector<Frame> stack;
+    int64_t b = 0, e = n, depth = 0;
+    for (;;) {
+      if (depth < limit && e - b > is_thresh) {
+        int64_t p = partition(A, b, e);
+        ++depth;
+        cnt.max_depth = std::max<uint64_t>(cnt.max_depth, (uint64_t)depth);
+        // Stack the larger side, continue with the smaller one; p itself is final.
+        if (p - b > e - (p + 1)) {
+          stack.push_back({b, p, depth});
+          b = p + 1;
+        } else {
+          stack.push_back({p + 1, e, depth});
+          e = p;
+        }
+      } else {
+        if (e - b > is_thresh) heap_sort(A, b, e);
+        else insertion_sort(A, b, e);
+        if (stack.empty()) break;
+        b = stack.back().b;
+        e = stack.back().e;
+        depth = stack.back().depth;
+        stack.pop_back();
+      }
+    }
+  }
+};
+
+template <class T, class Less>
+void run_sort(T* A, int64_t n, int rule, int64_t is_thresh, int64_t depth_limit, Counters& c) {
+  Sorter<T, Less> s{c, rule, std::max<int64_t>(is_thresh, 2), depth_limit};
+  s.sort(A, n);
+}
+
+template <class T, class Less>
+int64_t run_block_partition(T* A, int64_t n, int64_t pivot_pos, Counters& c) {
+  Sorter<T, Less> s{c, kMedianOf3, 16, -1};
+  return s.block_partition(A, 0, n, pivot_pos);
+}
+
+// Plain definition of a value partition: out = (elements < pivot, in input order)
+// followed by (elements >= pivot, in input order); returns count(< pivot).
+template <class T, class Less>
+int64_t run_partition_by_value(const T* keys, int64_t n, T pivot, T* out) {
+  Less less;
+  int64_t split = 0;
+  for (int64_t i = 0; i < n; ++i) split += less(keys[i], pivot);
+  int64_t lo = 0, hi = split;
+  for (int64_t i = 0; i < n; ++i) {
+    if (less(keys[i], pivot)) out[lo++] = keys[i];
+    else out[hi++] = keys[i];
+  }
+  return split;
+}
+
+template <class K, class KeyLess>
+void run_sort_pairs(K* keys, uint32_t* vals, int64_t n, int rule, Counters& c) {
+  std::vector<Pair<K>> a(n);
+  for (int64_t i = 0; i < n; ++i) a[i] = Pair<K>{keys[i], vals[i]};
+  run_sort<Pair<K>, LessPair<K, KeyLess>>(a.data(), n, rule, 16, -1, c);
+  for (int64_t i = 0; i < n; ++i) { keys[i] = a[i].key; vals[i] = a[i].val; }
+}
+
+void export_counters(const Counters& c, uint64_t* out) {
+  if (!out) return;
+  out[0] = c.comparisons;
+  out[1] = c.partitions;
+  out[2] = c.insertion_sorts;
+  out[3] = c.heap_sorts;
+  out[4] = c.depth_limit;
+  out[5] = c.max_depth;
+}
+
+}  // namespace
+
+extern "C" {
+
+// dtype: 0 = int32, 1 = int64, 2 = float64.  pivot_rule: 0 = median-of-3, 1 = sqrt(n).
+// counters (optional, 6 x uint64): comparisons, partitions, insertion sorts, heap sorts,
+// the depth limit used, the deepest partition level reached.
+int oracle_sort(void* keys, int64_t n, int32_t dtype, int32_t pivot_rule, int64_t is_thresh,
+                int64_t depth_limit, uint64_t* counters) {
+  if (n < 0 || (n > 0 && !keys) || pivot_rule < 0 || pivot_rule > 1) return -1;
+  Counters c;
+  switch (dtype) {
+    case 0: run_sort<int32_t, LessI32>((int32_t*)keys, n, pivot_rule, is_thresh, depth_limit, c); break;
+    case 1: run_sort<int64_t, LessI64>((int64_t*)keys, n, pivot_rule, is_thresh, depth_limit, c); break;
+    case 2: run_sort<double, LessF64>((double*)keys, n, pivot_rule, is_thresh, depth_limit, c); break;
+    default: return -1;
+  }
+  export_counters(c, counters);
+  return 0;
+}
+
+// Key-value sort, ordered by (key, payload).  Keys of the given dtype, uint32 payloads.
+int oracle_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, int32_t pivot_rule,
+                      uint64_t* counters) {
+  if (n < 0 || (n > 0 && (!keys || !vals)) || pivot_rule < 0 || pivot_rule > 1) return -1;
+  Counters c;
+  switch (dtype) {
+    case 0: run_sort_pairs<int32_t, LessI32>((int32_t*)keys, vals, n, pivot_rule, c); break;
+    case 1: run_sort_pairs<int64_t, LessI64>((int64_t*)keys, vals, n, pivot_rule, c); break;
+    case 2: run_sort_pairs<double, LessF64>((double*)keys, vals, n, pivot_rule, c); break;
+    default: return -1;
+  }
+  export_counters(c, counters);
+  return 0;
+}
+
+// Sorts every segment [seg_offsets[i], seg_offsets[i+1]) on its own.
+int oracle_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int32_t dtype,
+                          int32_t pivot_rule) {
+  if (nseg < 0 || (nseg > 0 && !seg_offsets)) return -1;
+  for (int64_t s = 0; s < nseg; ++s)
+    if (seg_offsets[s + 1] < seg_offsets[s] || seg_offsets[s] < 0) return -1;
+  const int64_t size = dtype == 0 ? 4 : 8;
+  for (int64_t s = 0; s < nseg; ++s) {
+    int rc = oracle_sort((char*)keys + seg_offsets[s] * size, seg_offsets[s + 1] - seg_offsets[s],
+                         dtype, pivot_rule, 16, -1, nullptr);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+// Algorithm 3 on the whole array keys[0, n) around the element at pivot_pos.
+// Returns the pivot's final position, or -1 on invalid arguments.
+int64_t oracle_block_partition(void* keys, int64_t n, int32_t dtype, int64_t pivot_pos,
+                               uint64_t* counters) {
+  if (n < 1 || !keys || pivot_pos < 0 || pivot_pos >= n) return -1;
+  Counters c;
+  int64_t p;
+  switch (dtype) {
+    case 0: p = run_block_partition<int32_t, LessI32>((int32_t*)keys, n, pivot_pos, c); break;
+    case 1: p = run_block_partition<int64_t, LessI64>((int64_t*)keys, n, pivot_pos, c); break;
+    case 2: p = run_block_partition<double, LessF64>((double*)keys, n, pivot_pos, c); break;
+    default: return -1;
+  }
+  export_counters(c, counters);
+  return p;
+}
+
+// Plain stable value partition (the definition behind bqs_partition).  pivot points to
+// one key of the given dtype.  Returns count(< pivot), or -1 on invalid arguments.
+int64_t oracle_partition_by_value(const void* keys, int64_t n, int32_t dtype, const void* pivot,
+                                  void* out) {
+  if (n < 0 || (n > 0 && (!keys || !out)) || !pivot) return -1;
+  switch (dtype) {
+    case 0: return run_partition_by_value<int32_t, LessI32>((const int32_t*)keys, n, *(const int32_t*)pivot, (int32_t*)out);
+    case 1: return run_partition_by_value<int64_t, LessI64>((const int64_t*)keys, n, *(const int64_t*)pivot, (int64_t*)out);
+    case 2: return run_partition_by_value<double, LessF64>((const double*)keys, n, *(const double*)pivot, (double*)out);
+    default: return -1;
+  }
+}
+
+}  // extern "C"
