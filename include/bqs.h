@@ -1,0 +1,168 @@
+/*
+ * bqs.h -- C ABI of the GB300 (sm_103a) data-parallel BlockQuicksort library.
+ *
+ * The method is BlockQuicksort (Edelkamp & Weiss, arXiv 1604.06697): Quicksort
+ * whose partitioning step first compares a whole block of keys with the pivot,
+ * keeps the outcomes in a buffer, and only then moves the keys (Sec. 3,
+ * Algorithm 3).  Here a block is a tile of keys held by one thread block; the
+ * comparison outcomes live in registers, local offsets come from warp ballots
+ * and population counts, tile offsets from a block scan, and each tile reserves
+ * its output ranges with one atomic before it scatters into a second buffer.
+ * Quicksort's main loop (Sec. 2, Algorithm 1) runs level by level over all
+ * unfinished segments at once; segments of at most the small-segment cutoff are
+ * finished by an in-shared-memory sorting network, standing in for the paper's
+ * Insertionsort.
+ *
+ * Conventions shared by every call
+ *   - Keys live in device memory and are owned by the caller.  Pointers to keys,
+ *     payloads and outputs must be 16-byte aligned (BQS_ERR_INVALID otherwise).
+ *   - dtype: BQS_INT32, BQS_INT64 or BQS_FLOAT64.  float64 keys are ordered by the
+ *     total order ord(x) = bits(x) ^ (sign ? ~0 : 1<<63): IEEE "<" on non-NaN
+ *     values except that -0.0 sorts before +0.0.  NaN keys are not supported
+ *     (the result is then an unspecified permutation of the input).
+ *   - n is a key count; 0 <= n < 2^32.  n = 0 and n = 1 are successful no-ops.
+ *   - stream is a cudaStream_t passed as an opaque pointer (NULL = the legacy
+ *     default stream).  Sorts are asynchronous on it unless stated otherwise.
+ *   - Scratch memory (a second key buffer and the segment work lists) comes from
+ *     the buffer given to bqs_set_workspace when one is set and large enough,
+ *     otherwise from cudaMallocAsync on `stream` (returned with cudaFreeAsync
+ *     on the same stream before the call returns).
+ *   - Return value: BQS_OK (0) or a negative bqs_status; bqs_status_string()
+ *     gives a description, including the CUDA error text for BQS_ERR_CUDA.
+ *   - Calls are thread-safe with respect to each other unless they share a
+ *     workspace set by bqs_set_workspace.
+ */
+#ifndef BQS_H_
+#define BQS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* bqs_stream_t; /* a cudaStream_t */
+
+typedef enum { BQS_INT32 = 0, BQS_INT64 = 1, BQS_FLOAT64 = 2 } bqs_dtype;
+
+typedef enum {
+  BQS_OK = 0,
+  BQS_ERR_INVALID = -1,     /* bad argument (size, alignment, dtype, overlap, offsets) */
+  BQS_ERR_NOMEM = -2,       /* scratch memory could not be obtained */
+  BQS_ERR_CUDA = -3,        /* a CUDA call or kernel launch failed */
+  BQS_ERR_TIMEOUT = -4,     /* a device-side bounded wait ran out */
+  BQS_ERR_UNSUPPORTED = -5  /* option or combination not provided */
+} bqs_status;
+
+/* A pivot value for bqs_partition.  dtype selects the member of v that is read. */
+typedef struct {
+  int32_t dtype;
+  int32_t reserved; /* must be 0 */
+  union {
+    int32_t i32;
+    int64_t i64;
+    double f64;
+  } v;
+} bqs_pivot;
+
+/*
+ * bqs_partition -- one partitioning step with a caller-given pivot.
+ * Paper: Sec. 2 ("Quicksort and improvements": the partitioner leaves elements
+ * <= pivot on the left and >= pivot on the right) and Sec. 3 / Algorithm 3 (the
+ * block-wise scan-then-rearrange procedure), done by all tiles at once.
+ *
+ *   keys   device, n keys of pivot->dtype, read only.
+ *   n      number of keys.
+ *   pivot  host pointer to the pivot value and its dtype.
+ *   out    device, n keys, written: out[0, *split) holds exactly the keys < pivot,
+ *          out[*split, n) the keys >= pivot (the keys == pivot come first in it).
+ *          The order inside each side is unspecified.  out must not overlap keys.
+ *   split  host pointer; receives count(keys < pivot).
+ * Synchronous: returns after `stream` has completed the work.
+ */
+int bqs_partition(const void* keys, int64_t n, const bqs_pivot* pivot, void* out,
+                  int64_t* split, bqs_stream_t stream);
+
+/*
+ * bqs_sort -- sorts keys[0, n) ascending, in place.
+ * Paper: Sec. 2 / Algorithm 1 (Quicksort main loop: choose a pivot, partition,
+ * recurse on both sides with the pivot excluded), Sec. 3 / Algorithm 3 (block
+ * partitioning), Sec. 2 and Sec. 4 (median-of-3 / median-of-sqrt(n) pivots,
+ * Introsort depth limit 2 log n + 3, small-array stopper).
+ * Asynchronous on `stream`.
+ */
+int bqs_sort(void* keys, int64_t n, int32_t dtype, bqs_stream_t stream);
+
+/*
+ * bqs_sort_segmented -- sorts every segment [seg_offsets[i], seg_offsets[i+1])
+ * of keys on its own, in place, i = 0 .. nseg-1, all in one level-synchronous
+ * pass over all segments (the batching of small arrays of Sec. 4, "Experiments").
+ *   seg_offsets  device, nseg+1 int64 values; must be non-decreasing with
+ *                seg_offsets[0] >= 0.  Empty segments are allowed.  A violation
+ *                found on the device is reported as BQS_ERR_INVALID.
+ * The host reads seg_offsets[nseg] once to size the scratch memory.
+ */
+int bqs_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int32_t dtype,
+                       bqs_stream_t stream);
+
+/*
+ * bqs_sort_pairs -- sorts (keys[i], vals[i]) pairs in place, ordered
+ * lexicographically by (key, payload), so the result is unique when payloads
+ * are distinct.  Paper: the same method as bqs_sort applied to a wider element
+ * (Sec. 4 sorts the 84-byte Record element by its first field the same way).
+ *   vals  device, n uint32 payloads, moved with their keys.
+ */
+int bqs_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, bqs_stream_t stream);
+
+/* Process-wide options, read at the start of each call. */
+typedef enum {
+  BQS_OPT_PIVOT = 0,        /* 0 = median-of-3 (default), 1 = median of a sqrt(n) sample */
+  BQS_OPT_SMALL_CUTOFF = 1, /* small-segment cutoff C, 2 .. 2048 (default 2048) */
+  BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
+  BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */
+  BQS_OPT_TILE = 4,         /* partition tile variant: 0 = default, 1..N autotuner choices */
+  BQS_OPT_LOCAL_CUTOFF = 5  /* segments up to this size are sorted inside one thread block */
+} bqs_option;
+
+int bqs_set_option(int32_t opt, int64_t value);
+int bqs_get_option(int32_t opt, int64_t* value);
+
+/* Bytes of scratch a call needs: n keys, nseg segments (0 for a single array). */
+int bqs_workspace_bytes(int64_t n, int32_t dtype, int32_t with_payload, int64_t nseg,
+                        int64_t* bytes);
+
+/*
+ * Sets (ptr != NULL) or clears (ptr == NULL) a caller-owned device workspace used
+ * by later calls that fit into it.  The caller keeps ownership, must keep it alive
+ * while calls that may use it are in flight, and must not let two such calls run
+ * concurrently.
+ */
+int bqs_set_workspace(void* ptr, int64_t bytes);
+
+/* Counters of the calling thread's last sort call. */
+typedef struct {
+  int64_t levels;            /* partition levels run */
+  int64_t partition_launches;
+  int64_t active_keys;       /* sum over levels of keys in partitioned segments */
+  int64_t moved_keys;        /* of those, keys scattered (< or > pivot) */
+  int64_t equal_keys;        /* keys found equal to their segment's pivot */
+  int64_t small_segments;    /* segments finished by the small-segment sort */
+  int64_t small_keys;
+  int64_t local_segments;    /* segments finished inside one thread block */
+  int64_t local_keys;
+  int64_t fallback_pivots;   /* depth-limit fallbacks */
+  int64_t kernel_launches;   /* kernels this library launched for the call */
+  double partition_ms;       /* sum of timed partition launches (BQS_OPT_TIMING) */
+  double partition_bytes;    /* algorithmic bytes of those launches */
+} bqs_stats;
+
+int bqs_get_stats(bqs_stats* out);
+
+/* Static description of a status code (thread-local detail for BQS_ERR_CUDA). */
+const char* bqs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BQS_H_ */

@@ -1,1 +1,143 @@
-"""GB300-native (sm_103a) data-parallel BlockQuicksort."""
+"""GB300-native (sm_103a) data-parallel BlockQuicksort.
+
+A thin binding over the C ABI of ``libbqs.so`` (see ``include/bqs.h``).  The
+functions take CUDA tensors and only marshal arguments: every step of every
+sort runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _native
+
+BQS_OK = 0
+DTYPE_CODES = {"int32": 0, "int64": 1, "float64": 2}
+OPTIONS = {"pivot": 0, "small_cutoff": 1, "depth_limit": 2, "timing": 3, "tile": 4,
+           "local_cutoff": 5}
+
+
+class BqsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _native.lib().bqs_status_string(status).decode()
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+def _check(status: int, where: str) -> None:
+    if status != BQS_OK:
+        raise BqsError(status, where)
+
+
+def _dtype_code(t) -> int:
+    name = str(t.dtype).replace("torch.", "")
+    if name not in DTYPE_CODES:
+        raise TypeError(f"unsupported key dtype {t.dtype}")
+    return DTYPE_CODES[name]
+
+
+def _stream_ptr(t, stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected contiguous CUDA tensors")
+
+
+def sort(keys, stream=None):
+    """Sorts a contiguous CUDA tensor of int32/int64/float64 keys in place."""
+    _require_cuda(keys)
+    _check(_native.lib().bqs_sort(keys.data_ptr(), keys.numel(), _dtype_code(keys),
+                                  _stream_ptr(keys, stream)), "bqs_sort")
+    return keys
+
+
+def sort_pairs(keys, vals, stream=None):
+    """Sorts (key, uint32 payload) pairs in place by (key, payload).
+
+    ``vals`` is an int32 or uint32 tensor whose bits are the payloads.
+    """
+    _require_cuda(keys, vals)
+    if vals.numel() != keys.numel() or vals.element_size() != 4:
+        raise ValueError("vals must hold one 32-bit payload per key")
+    _check(_native.lib().bqs_sort_pairs(keys.data_ptr(), vals.data_ptr(), keys.numel(),
+                                        _dtype_code(keys), _stream_ptr(keys, stream)),
+           "bqs_sort_pairs")
+    return keys, vals
+
+
+def sort_segmented(keys, seg_offsets, stream=None):
+    """Sorts every segment [off[i], off[i+1]) of ``keys`` in place (int64 offsets)."""
+    import torch
+    _require_cuda(keys, seg_offsets)
+    if seg_offsets.dtype != torch.int64:
+        raise TypeError("seg_offsets must be int64")
+    _check(_native.lib().bqs_sort_segmented(keys.data_ptr(), seg_offsets.data_ptr(),
+                                            seg_offsets.numel() - 1, _dtype_code(keys),
+                                            _stream_ptr(keys, stream)), "bqs_sort_segmented")
+    return keys
+
+
+def partition(keys, pivot, out=None, stream=None):
+    """Partitions ``keys`` around ``pivot`` into ``out``; returns (out, split).
+
+    out[:split] holds exactly the keys < pivot, out[split:] the keys >= pivot.
+    """
+    import torch
+    _require_cuda(keys)
+    if out is None:
+        out = torch.empty_like(keys)
+    _require_cuda(out)
+    code = _dtype_code(keys)
+    pv = _native.Pivot()
+    pv.dtype = code
+    pv.reserved = 0
+    if code == 0:
+        pv.v.i32 = int(pivot)
+    elif code == 1:
+        pv.v.i64 = int(pivot)
+    else:
+        pv.v.f64 = float(pivot)
+    split = ctypes.c_int64(0)
+    _check(_native.lib().bqs_partition(keys.data_ptr(), keys.numel(), ctypes.byref(pv),
+                                       out.data_ptr(), ctypes.byref(split),
+                                       _stream_ptr(keys, stream)), "bqs_partition")
+    return out, int(split.value)
+
+
+def set_option(name: str, value: int) -> None:
+    _check(_native.lib().bqs_set_option(OPTIONS[name], int(value)), f"bqs_set_option({name})")
+
+
+def get_option(name: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(_native.lib().bqs_get_option(OPTIONS[name], ctypes.byref(v)), f"bqs_get_option({name})")
+    return int(v.value)
+
+
+def workspace_bytes(n: int, dtype: str, with_payload: bool = False, nseg: int = 0) -> int:
+    v = ctypes.c_int64(0)
+    _check(_native.lib().bqs_workspace_bytes(n, DTYPE_CODES[dtype], int(with_payload), nseg,
+                                             ctypes.byref(v)), "bqs_workspace_bytes")
+    return int(v.value)
+
+
+def set_workspace(buf) -> None:
+    """Uses a caller-owned CUDA buffer (uint8 tensor) as scratch; None clears it."""
+    if buf is None:
+        _check(_native.lib().bqs_set_workspace(None, 0), "bqs_set_workspace")
+    else:
+        _check(_native.lib().bqs_set_workspace(buf.data_ptr(), buf.numel() * buf.element_size()),
+               "bqs_set_workspace")
+
+
+def stats() -> dict:
+    """Counters of this thread's last sort call."""
+    s = _native.Stats()
+    _check(_native.lib().bqs_get_stats(ctypes.byref(s)), "bqs_get_stats")
+    return {name: getattr(s, name) for name, _ in _native.Stats._fields_}

@@ -1,0 +1,273 @@
+// C ABI of the BlockQuicksort library: argument checks, options, workspace, statistics,
+// and dispatch to the per-dtype drivers.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "bqs.h"
+#include "bqs_driver.cuh"
+#include "bqs_internal.h"
+
+namespace bqs {
+
+namespace {
+std::mutex g_opt_mu;
+Options g_opt;
+std::mutex g_ws_mu;
+void* g_ws = nullptr;
+int64_t g_ws_bytes = 0;
+thread_local Stats t_stats;
+thread_local char t_err[320];
+thread_local Ctrl* t_pinned = nullptr;
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
+
+Options snapshot_options() {
+  std::lock_guard<std::mutex> g(g_opt_mu);
+  return g_opt;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+constexpr int64_t kMaxN = (int64_t)0xFFFFFFFFll;  // segment cursors hold 32-bit counts
+
+int key_size(int32_t dtype) { return dtype == BQS_INT32 ? 4 : 8; }
+
+int dispatch(int32_t dtype, const Call& c) {
+  t_stats = Stats{};
+  switch (dtype) {
+    case BQS_INT32: return run_i32(c, t_stats);
+    case BQS_INT64: return run_i64(c, t_stats);
+    case BQS_FLOAT64: return run_f64(c, t_stats);
+    default: return kErrInvalid;
+  }
+}
+}  // namespace
+
+int fail_cuda(cudaError_t e, const char* what) {
+  std::snprintf(t_err, sizeof t_err, "CUDA error in %s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return kErrCuda;
+}
+
+void user_workspace(void** ptr, int64_t* bytes) {
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  *ptr = g_ws;
+  *bytes = g_ws_bytes;
+}
+
+// Keeps freed stream-ordered allocations in the device's default pool, so repeated
+// calls do not return memory to the driver between sorts.
+void prepare_mempool() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> g(mu);
+  for (int d : done)
+    if (d == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
+Ctrl* pinned_ctrl() {
+  if (!t_pinned) {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, sizeof(Ctrl)) != cudaSuccess) {
+      cudaGetLastError();
+      static thread_local Ctrl fallback;  // pageable: copies still complete on sync
+      return &fallback;
+    }
+    t_pinned = (Ctrl*)p;
+  }
+  return t_pinned;
+}
+
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() { return t_events; }
+
+}  // namespace bqs
+
+using namespace bqs;
+
+extern "C" {
+
+int bqs_sort(void* keys, int64_t n, int32_t dtype, bqs_stream_t stream) {
+  if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || n < 0 || n > kMaxN) return BQS_ERR_INVALID;
+  t_stats = Stats{};
+  if (n <= 1) return BQS_OK;
+  if (!keys || !aligned16(keys)) return BQS_ERR_INVALID;
+  Call c;
+  c.keys = keys;
+  c.n = n;
+  c.stream = stream;
+  c.opt = snapshot_options();
+  return dispatch(dtype, c);
+}
+
+int bqs_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, bqs_stream_t stream) {
+  if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || n < 0 || n > kMaxN) return BQS_ERR_INVALID;
+  t_stats = Stats{};
+  if (n <= 1) return BQS_OK;
+  if (!keys || !vals || !aligned16(keys) || !aligned16(vals)) return BQS_ERR_INVALID;
+  Call c;
+  c.keys = keys;
+  c.vals = vals;
+  c.n = n;
+  c.stream = stream;
+  c.opt = snapshot_options();
+  return dispatch(dtype, c);
+}
+
+int bqs_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int32_t dtype,
+                       bqs_stream_t stream) {
+  if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || nseg < 0) return BQS_ERR_INVALID;
+  t_stats = Stats{};
+  if (nseg == 0) return BQS_OK;
+  if (!seg_offsets || ((uintptr_t)seg_offsets & 7u)) return BQS_ERR_INVALID;
+  int64_t total = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&total, seg_offsets + nseg, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "reading seg_offsets[nseg]");
+  if (total < 0 || total > kMaxN) return BQS_ERR_INVALID;
+  if (total > 0 && (!keys || !aligned16(keys))) return BQS_ERR_INVALID;
+  Call c;
+  c.keys = keys;
+  c.n = total;
+  c.seg_offsets = seg_offsets;
+  c.nseg = nseg;
+  c.stream = stream;
+  c.opt = snapshot_options();
+  return dispatch(dtype, c);
+}
+
+int bqs_partition(const void* keys, int64_t n, const bqs_pivot* pivot, void* out, int64_t* split,
+                  bqs_stream_t stream) {
+  if (!pivot || !split || pivot->reserved != 0) return BQS_ERR_INVALID;
+  const int32_t dtype = pivot->dtype;
+  if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || n < 0 || n > kMaxN) return BQS_ERR_INVALID;
+  t_stats = Stats{};
+  if (n == 0) {
+    *split = 0;
+    return BQS_OK;
+  }
+  if (!keys || !out || !aligned16(keys) || !aligned16(out)) return BQS_ERR_INVALID;
+  const uintptr_t a = (uintptr_t)keys, b = (uintptr_t)out, bytes = (uintptr_t)n * key_size(dtype);
+  if (a < b + bytes && b < a + bytes) return BQS_ERR_INVALID;
+  Call c;
+  c.keys = (void*)keys;
+  c.n = n;
+  c.partition_only = true;
+  c.out = out;
+  c.split = split;
+  c.stream = stream;
+  c.opt = snapshot_options();
+  if (dtype == BQS_INT32) c.pivot_raw = (uint32_t)pivot->v.i32;
+  else if (dtype == BQS_INT64) c.pivot_raw = (uint64_t)pivot->v.i64;
+  else std::memcpy(&c.pivot_raw, &pivot->v.f64, 8);
+  return dispatch(dtype, c);
+}
+
+int bqs_set_option(int32_t opt, int64_t value) {
+  std::lock_guard<std::mutex> g(g_opt_mu);
+  switch (opt) {
+    case BQS_OPT_PIVOT:
+      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      g_opt.pivot_rule = value;
+      return BQS_OK;
+    case BQS_OPT_SMALL_CUTOFF:
+      if (value < 2 || value > kMaxSmall) return BQS_ERR_INVALID;
+      g_opt.small_cutoff = value;
+      return BQS_OK;
+    case BQS_OPT_DEPTH_LIMIT:
+      if (value < -1 || value > 100000) return BQS_ERR_INVALID;
+      g_opt.depth_limit = value;
+      return BQS_OK;
+    case BQS_OPT_TIMING:
+      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      g_opt.timing = value;
+      return BQS_OK;
+    case BQS_OPT_TILE:
+      if (value < 0 || value > 3) return BQS_ERR_INVALID;
+      g_opt.tile_variant = value;
+      return BQS_OK;
+    case BQS_OPT_LOCAL_CUTOFF:
+      if (value < 0 || value > (1 << 20)) return BQS_ERR_INVALID;
+      g_opt.local_cutoff = value;
+      return BQS_OK;
+    default:
+      return BQS_ERR_UNSUPPORTED;
+  }
+}
+
+int bqs_get_option(int32_t opt, int64_t* value) {
+  if (!value) return BQS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_opt_mu);
+  switch (opt) {
+    case BQS_OPT_PIVOT: *value = g_opt.pivot_rule; return BQS_OK;
+    case BQS_OPT_SMALL_CUTOFF: *value = g_opt.small_cutoff; return BQS_OK;
+    case BQS_OPT_DEPTH_LIMIT: *value = g_opt.depth_limit; return BQS_OK;
+    case BQS_OPT_TIMING: *value = g_opt.timing; return BQS_OK;
+    case BQS_OPT_TILE: *value = g_opt.tile_variant; return BQS_OK;
+    case BQS_OPT_LOCAL_CUTOFF: *value = g_opt.local_cutoff; return BQS_OK;
+    default: return BQS_ERR_UNSUPPORTED;
+  }
+}
+
+int bqs_workspace_bytes(int64_t n, int32_t dtype, int32_t with_payload, int64_t nseg,
+                        int64_t* bytes) {
+  if (!bytes || n < 0 || n > kMaxN || nseg < 0 || dtype < BQS_INT32 || dtype > BQS_FLOAT64)
+    return BQS_ERR_INVALID;
+  const Options o = snapshot_options();
+  const Layout L = plan_layout(n, key_size(dtype), with_payload != 0, nseg, (int)o.small_cutoff, true);
+  *bytes = (int64_t)L.total;
+  return BQS_OK;
+}
+
+int bqs_set_workspace(void* ptr, int64_t bytes) {
+  if (ptr && (bytes <= 0 || ((uintptr_t)ptr & 255u))) return BQS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  g_ws = ptr;
+  g_ws_bytes = ptr ? bytes : 0;
+  return BQS_OK;
+}
+
+int bqs_get_stats(bqs_stats* out) {
+  if (!out) return BQS_ERR_INVALID;
+  const Stats& s = t_stats;
+  out->levels = s.levels;
+  out->partition_launches = s.partition_launches;
+  out->active_keys = s.active_keys;
+  out->moved_keys = s.moved_keys;
+  out->equal_keys = s.equal_keys;
+  out->small_segments = s.small_segments;
+  out->small_keys = s.small_keys;
+  out->local_segments = s.local_segments;
+  out->local_keys = s.local_keys;
+  out->fallback_pivots = s.fallback_pivots;
+  out->kernel_launches = s.kernel_launches;
+  out->partition_ms = s.partition_ms;
+  out->partition_bytes = (double)(s.active_keys + s.moved_keys) * s.partition_bytes_per_key;
+  return BQS_OK;
+}
+
+const char* bqs_status_string(int status) {
+  switch (status) {
+    case BQS_OK: return "ok";
+    case BQS_ERR_INVALID: return "invalid argument";
+    case BQS_ERR_NOMEM: return "out of device memory for scratch";
+    case BQS_ERR_CUDA: return t_err[0] ? t_err : "CUDA error";
+    case BQS_ERR_TIMEOUT: return "device-side wait timed out";
+    case BQS_ERR_UNSUPPORTED: return "unsupported option or combination";
+    case kErrInternal: return "internal work list overflow";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Shared definitions of the sm_103a BlockQuicksort kernels and their host driver.
+//
+// Data layout in HBM
+//   key[0]  the caller's keys (final output of sorts)
+//   key[1]  a second key buffer of the same size (ping-pong partner)
+//   val[*]  the same for uint32 payloads of key-value sorts
+// A segment is a contiguous index range [off, off+len) whose keys sit in key[parity].
+// One partition level moves every key of every large segment from key[parity] into
+// key[parity^1]; finished keys (the class equal to a pivot, and small segments after
+// their sorting network) are written straight into the final buffer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bqs {
+
+// ---- key types ---------------------------------------------------------------------
+// Keys travel as raw bits U and are compared through an order-preserving unsigned
+// image ord(x): one unsigned comparison serves int32, int64 and float64.  For float64,
+// ord(x) = bits ^ (sign ? ~0 : 1<<63), a total order equal to IEEE "<" on non-NaN
+// values except -0.0 < +0.0.
+
+struct KeyI32 {
+  using U = uint32_t;
+  static constexpr int kDtype = 0;
+  __host__ __device__ static __forceinline__ U ord(U x) { return x ^ 0x80000000u; }
+  __host__ __device__ static __forceinline__ U unord(U x) { return x ^ 0x80000000u; }
+};
+
+struct KeyI64 {
+  using U = uint64_t;
+  static constexpr int kDtype = 1;
+  __host__ __device__ static __forceinline__ U ord(U x) { return x ^ (1ull << 63); }
+  __host__ __device__ static __forceinline__ U unord(U x) { return x ^ (1ull << 63); }
+};
+
+struct KeyF64 {
+  using U = uint64_t;
+  static constexpr int kDtype = 2;
+  __host__ __device__ static __forceinline__ U ord(U x) {
+    U m = (U)((int64_t)x >> 63);           // all ones for negative values
+    return x ^ (m | (1ull << 63));
+  }
+  __host__ __device__ static __forceinline__ U unord(U x) {
+    U m = (U)((int64_t)x >> 63);           // all ones when the order image has its top bit
+    return x ^ (~m | (1ull << 63));
+  }
+};
+
+// Strict order on (ord key, payload); payloads only take part for key-value sorts.
+template <bool PAIRS, class U>
+__device__ __forceinline__ bool elem_less(U ka, uint32_t va, U kb, uint32_t vb) {
+  if constexpr (PAIRS) return ka < kb || (ka == kb && va < vb);
+  else return ka < kb;
+}
+
+// ---- work lists ------------------------------------------------------------------
+
+// A segment still to be partitioned.
+struct Seg {
+  int64_t off;
+  int64_t len;
+  uint64_t pkey;    // pivot: raw key bits (zero-extended)
+  uint32_t pval;    // pivot payload (key-value sorts)
+  int32_t depth;    // partition levels above this segment
+  int32_t parity;   // its keys are in key[parity]
+  uint32_t tile0;   // first tile of this segment in the level's tile space
+};
+
+// A segment to be finished by one thread block (small-segment sort).
+struct Run {
+  int64_t off;
+  int64_t len;
+  int32_t parity;
+  int32_t pad;
+};
+
+// A range of keys equal to a segment's pivot: written with the pivot value.
+struct Fill {
+  int64_t off;
+  int64_t len;
+  uint64_t pkey;
+  uint32_t pval;
+  uint32_t tile0;
+};
+
+// Counts of the lists that one level produces (count | tiles << 32 where tiled).
+struct ListCounts {
+  unsigned long long large;
+  unsigned long long fill;
+  unsigned long long large_keys;  // sum of the large segments' lengths
+  unsigned int small;
+  unsigned int local;
+};
+
+struct Ctrl {
+  ListCounts lists[2];
+  int status;
+  int pad;
+  unsigned long long moved_keys;
+  unsigned long long equal_keys;
+  unsigned long long small_segs;
+  unsigned long long small_keys;
+  unsigned long long local_segs;
+  unsigned long long local_keys;
+  unsigned long long fallbacks;
+};
+
+struct Bufs {
+  void* key[2];
+  uint32_t* val[2];
+  void* final_key;
+  uint32_t* final_val;
+};
+
+struct Lists {
+  Seg* large[2];
+  unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
+  Run* small[2];
+  Run* local[2];
+  Fill* fill[2];
+  uint32_t cap_large, cap_run, cap_fill;
+};
+
+struct Params {
+  Bufs b;
+  Lists l;
+  Ctrl* ctrl;
+  int p;              // parity of the lists consumed by this level
+  int pivot_rule;     // 0 = median-of-3, 1 = median of a sqrt(n) sample
+  int small_cutoff;   // segments of at most this many keys go to the sorting network
+  int local_cutoff;   // segments of at most this many keys are finished by one block
+  int depth_limit;    // partition levels before the depth fallback pivot
+  int route_children; // 0: a single partition step (no recursion)
+  int tile;           // keys per partition tile (for tile counts)
+  int pad;
+};
+
+// Device status codes (mirrors the public bqs_status values).
+constexpr int kStatusInvalid = -1;
+constexpr int kStatusOverflow = -6;  // an internal list overflowed its capacity
+
+constexpr int kFillTile = 8192;      // keys per fill task
+constexpr int kMaxSmall = 2048;      // largest small-segment cutoff
+constexpr int kMaxSample = 2047;     // largest pivot sample
+
+}  // namespace bqs

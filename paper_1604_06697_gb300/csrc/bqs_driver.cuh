@@ -1,0 +1,329 @@
+// Host driver of the level-synchronous BlockQuicksort (one instantiation per key type).
+//
+// The Quicksort main loop of the paper (Sec. 2, Algorithm 1, with an explicit stack) is
+// replaced by work lists processed breadth-first: every level partitions all unfinished
+// large segments at once, and the children it produces are the next level's work.  The
+// host only reads the next level's list counts (32 bytes) between levels.
+#pragma once
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "bqs_internal.h"
+#include "bqs_kernels.cuh"
+
+namespace bqs {
+
+// ---- scratch layout ----------------------------------------------------------------------
+
+struct Layout {
+  size_t alt_key = 0, alt_val = 0, ctrl = 0;
+  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
+  size_t total = 0;
+  uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Capacities: large segments are longer than the small cutoff and disjoint, so a level
+// holds at most n/(C+1) of them; each yields at most two children (or, at the first
+// level, one entry per caller segment).
+inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff,
+                          bool need_alt) {
+  Layout L;
+  const uint64_t cap_large = (uint64_t)n / (uint64_t)(small_cutoff + 1) + 2;
+  const uint64_t cap_run = std::max<uint64_t>(2 * cap_large, (uint64_t)nseg) + 2;
+  L.cap_large = (uint32_t)std::min<uint64_t>(cap_large, 0xFFFFFFF0ull);
+  L.cap_run = (uint32_t)std::min<uint64_t>(cap_run, 0xFFFFFFF0ull);
+  L.cap_fill = L.cap_large;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+  L.ctrl = take(sizeof(Ctrl));
+  if (need_alt) {
+    L.alt_key = take((size_t)n * key_size);
+    if (pairs) L.alt_val = take((size_t)n * 4);
+  }
+  for (int i = 0; i < 2; ++i) {
+    L.large[i] = take((size_t)L.cap_large * sizeof(Seg));
+    L.cursor[i] = take((size_t)L.cap_large * 8);
+    L.small[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.local[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.fill[i] = take((size_t)L.cap_fill * sizeof(Fill));
+  }
+  L.total = o;
+  return L;
+}
+
+// Scratch for one call: the caller-set workspace when it fits, else stream-ordered
+// allocation returned on the same stream.
+struct Scratch {
+  char* base = nullptr;
+  bool owned = false;
+  cudaStream_t st = nullptr;
+  ~Scratch() {
+    if (owned && base) cudaFreeAsync(base, st);
+  }
+};
+
+inline int acquire_scratch(Scratch& s, size_t bytes, cudaStream_t st) {
+  s.st = st;
+  void* ws = nullptr;
+  int64_t ws_bytes = 0;
+  user_workspace(&ws, &ws_bytes);
+  if (ws && (size_t)ws_bytes >= bytes) {
+    s.base = (char*)ws;
+    s.owned = false;
+    return kOk;
+  }
+  prepare_mempool();
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? kErrNoMem : fail_cuda(e, "cudaMallocAsync");
+  }
+  s.base = (char*)p;
+  s.owned = true;
+  return kOk;
+}
+
+// ---- partition kernel variants -------------------------------------------------------------
+
+struct Variant {
+  int threads, kpt;
+  const void* fn;
+  void (*launch)(const Params&, int grid, cudaStream_t);
+};
+
+template <class KT, bool PAIRS, int T, int K, int MINB>
+void launch_partition(const Params& P, int grid, cudaStream_t st) {
+  k_partition<KT, PAIRS, T, K, MINB><<<grid, T, 0, st>>>(P);
+}
+
+template <class KT, bool PAIRS, int T, int K, int MINB>
+Variant make_variant() {
+  return Variant{T, K, (const void*)k_partition<KT, PAIRS, T, K, MINB>,
+                 &launch_partition<KT, PAIRS, T, K, MINB>};
+}
+
+// Tile shapes offered to the autotuner: keys per tile = threads * keys-per-thread.
+template <class KT, bool PAIRS>
+const std::vector<Variant>& variants() {
+  static const std::vector<Variant> v = [] {
+    std::vector<Variant> r;
+    if constexpr (sizeof(typename KT::U) == 4) {
+      r.push_back(make_variant<KT, PAIRS, 256, 16, 4>());
+      r.push_back(make_variant<KT, PAIRS, 256, 32, 2>());
+      r.push_back(make_variant<KT, PAIRS, 512, 16, 2>());
+      r.push_back(make_variant<KT, PAIRS, 128, 32, 4>());
+    } else {
+      r.push_back(make_variant<KT, PAIRS, 256, 8, 4>());
+      r.push_back(make_variant<KT, PAIRS, 256, 16, 2>());
+      r.push_back(make_variant<KT, PAIRS, 512, 8, 2>());
+      r.push_back(make_variant<KT, PAIRS, 128, 16, 4>());
+    }
+    return r;
+  }();
+  return v;
+}
+
+// Persistent grid of a kernel: resident blocks per SM times the SM count.
+inline int persistent_grid(const void* fn, int threads) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  for (auto& e : cache)
+    if (e.first == fn) return e.second;
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+  const int g_ = std::max(1, sms * std::max(1, per));
+  cache.emplace_back(fn, g_);
+  return g_;
+}
+
+inline int sm_count() {
+  static int sms = [] {
+    int dev = 0, s = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, s);
+  }();
+  return sms;
+}
+
+// ---- the level loop --------------------------------------------------------------------------
+
+#define BQS_CK(call)                                              \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #call);           \
+  } while (0)
+
+template <class KT, bool PAIRS>
+int run_call(const Call& c, Stats& st) {
+  using U = typename KT::U;
+  const cudaStream_t s = (cudaStream_t)c.stream;
+  const auto& vars = variants<KT, PAIRS>();
+  const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
+  const int tile = var.threads * var.kpt;
+  const int small_cutoff = c.partition_only ? 1 : (int)c.opt.small_cutoff;
+  // Segments up to local_cutoff would be finished by one thread block; until that kernel
+  // exists every segment above the small cutoff is partitioned.
+  const int local_cutoff = small_cutoff;
+
+  const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only);
+  Scratch scratch;
+  int rc = acquire_scratch(scratch, L.total, s);
+  if (rc) return rc;
+  char* w = scratch.base;
+
+  Params P{};
+  P.ctrl = (Ctrl*)(w + L.ctrl);
+  if (c.partition_only) {
+    P.b.key[0] = c.keys; P.b.key[1] = c.out; P.b.final_key = c.out;
+  } else {
+    P.b.key[0] = c.keys; P.b.key[1] = w + L.alt_key; P.b.final_key = c.keys;
+    if (PAIRS) {
+      P.b.val[0] = c.vals; P.b.val[1] = (uint32_t*)(w + L.alt_val); P.b.final_val = c.vals;
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    P.l.large[i] = (Seg*)(w + L.large[i]);
+    P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
+    P.l.small[i] = (Run*)(w + L.small[i]);
+    P.l.local[i] = (Run*)(w + L.local[i]);
+    P.l.fill[i] = (Fill*)(w + L.fill[i]);
+  }
+  P.l.cap_large = L.cap_large; P.l.cap_run = L.cap_run; P.l.cap_fill = L.cap_fill;
+  P.pivot_rule = c.opt.pivot_rule;
+  P.small_cutoff = small_cutoff;
+  P.local_cutoff = local_cutoff;
+  P.route_children = c.partition_only ? 0 : 1;
+  P.tile = tile;
+  {
+    int64_t top = c.n;  // depth limit 2*floor(log2 n)+3 of the largest array (Sec. 2)
+    int lg = 0;
+    while (top > 1) { top >>= 1; ++lg; }
+    P.depth_limit = c.opt.depth_limit >= 0 ? (int)c.opt.depth_limit : 2 * lg + 3;
+  }
+
+  Ctrl* host = pinned_ctrl();
+  BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
+
+  ListCounts cur{};
+  if (c.partition_only) {
+    k_init_partition<KT><<<1, 32, 0, s>>>(P, c.n, c.pivot_raw);
+    st.kernel_launches += 1;
+    cur.large = 1ull | ((unsigned long long)((c.n - 1) / tile + 1) << 32);
+    cur.large_keys = (unsigned long long)c.n;
+  } else if (c.seg_offsets) {
+    const int g = (int)std::min<int64_t>((c.nseg + 255) / 256, 4 * sm_count());
+    k_init_segments<KT><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
+    st.kernel_launches += 1;
+    BQS_CK(cudaGetLastError());
+    BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BQS_CK(cudaStreamSynchronize(s));
+    if (host->status) return host->status == kStatusInvalid ? kErrInvalid : kErrInternal;
+    cur = host->lists[0];
+  } else {
+    k_init_single<KT><<<1, 32, 0, s>>>(P, c.n);
+    st.kernel_launches += 1;
+    if (c.n <= small_cutoff) cur.small = 1;
+    else if (c.n <= local_cutoff) cur.local = 1;
+    else {
+      cur.large = 1ull | ((unsigned long long)((c.n - 1) / tile + 1) << 32);
+      cur.large_keys = (unsigned long long)c.n;
+    }
+  }
+  BQS_CK(cudaGetLastError());
+
+  const int sms = sm_count();
+  const int part_grid_max = persistent_grid(var.fn, var.threads);
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
+  size_t ev_used = 0;
+
+  // Every level removes the pivot class of each segment, and past the depth limit the
+  // range-midpoint pivot halves the key range: more levels than this means a bug.
+  const int max_levels = P.depth_limit + 8 * (int)sizeof(U) + 40;
+  for (int level = 0;; ++level) {
+    if (level > max_levels) return kErrInternal;
+    P.p = level & 1;
+    const uint32_t nlarge = (uint32_t)cur.large, ntiles = (uint32_t)(cur.large >> 32);
+    if (nlarge) {
+      st.levels += 1;
+      st.partition_launches += 1;
+      st.active_keys += (int64_t)cur.large_keys;
+      if (!c.partition_only) {
+        k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(nlarge, 8 * sms), 256, 0, s>>>(P);
+        st.kernel_launches += 1;
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c.opt.timing) {
+        if (ev_used == evs.size()) {
+          cudaEvent_t a, b;
+          BQS_CK(cudaEventCreate(&a));
+          BQS_CK(cudaEventCreate(&b));
+          evs.emplace_back(a, b);
+        }
+        e0 = evs[ev_used].first; e1 = evs[ev_used].second;
+        ++ev_used;
+        BQS_CK(cudaEventRecord(e0, s));
+      }
+      var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s);
+      if (c.opt.timing) BQS_CK(cudaEventRecord(e1, s));
+      k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
+      k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
+      st.kernel_launches += 3;
+    }
+    if (cur.small) {
+      st.small_segments += cur.small;
+      k_small_sort<KT, PAIRS><<<(int)std::min<uint32_t>(cur.small, 16 * sms), 256, 0, s>>>(P, P.p);
+      st.kernel_launches += 1;
+    }
+    BQS_CK(cudaGetLastError());
+    if (!nlarge) break;
+    BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BQS_CK(cudaStreamSynchronize(s));
+    if (host->status) return host->status == kStatusInvalid ? kErrInvalid : kErrInternal;
+    if (c.partition_only) {
+      // split = #(< pivot); the cursor of the single segment holds it.
+      unsigned long long cursor = 0;
+      BQS_CK(cudaMemcpyAsync(&cursor, P.l.cursor[0], 8, cudaMemcpyDeviceToHost, s));
+      BQS_CK(cudaStreamSynchronize(s));
+      *c.split = (int64_t)(uint32_t)cursor;
+      break;
+    }
+    cur = host->lists[P.p ^ 1];
+  }
+  st.moved_keys = (int64_t)host->moved_keys;
+  st.equal_keys = (int64_t)host->equal_keys;
+  st.fallback_pivots = (int64_t)host->fallbacks;
+  st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
+  if (c.opt.timing && ev_used) {
+    BQS_CK(cudaStreamSynchronize(s));
+    double ms = 0;
+    for (size_t i = 0; i < ev_used; ++i) {
+      float t = 0;
+      BQS_CK(cudaEventElapsedTime(&t, evs[i].first, evs[i].second));
+      ms += t;
+    }
+    st.partition_ms = ms;
+  }
+  return kOk;
+}
+
+#undef BQS_CK
+
+// Explicit instantiation helper used by the per-dtype translation units.
+#define BQS_INSTANTIATE(KT, NAME)                                                  \
+  int NAME(const Call& c, Stats& st) {                                             \
+    return c.vals ? run_call<KT, true>(c, st) : run_call<KT, false>(c, st);        \
+  }
+
+}  // namespace bqs

@@ -1,0 +1,65 @@
+// Internal declarations shared by the C-ABI front end (bqs_api.cu) and the per-dtype
+// driver translation units.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace bqs {
+
+struct Ctrl;
+
+constexpr int kOk = 0;
+constexpr int kErrInvalid = -1;
+constexpr int kErrNoMem = -2;
+constexpr int kErrCuda = -3;
+constexpr int kErrTimeout = -4;
+constexpr int kErrUnsupported = -5;
+constexpr int kErrInternal = -6;
+
+struct Options {
+  int64_t pivot_rule = 0;
+  int64_t small_cutoff = 2048;
+  int64_t depth_limit = -1;
+  int64_t timing = 0;
+  int64_t tile_variant = 0;
+  int64_t local_cutoff = 0;
+};
+
+struct Call {
+  void* keys = nullptr;
+  uint32_t* vals = nullptr;            // key-value sorts
+  int64_t n = 0;                       // total keys
+  const int64_t* seg_offsets = nullptr;
+  int64_t nseg = 0;
+  bool partition_only = false;         // bqs_partition
+  void* out = nullptr;
+  uint64_t pivot_raw = 0;
+  int64_t* split = nullptr;
+  void* stream = nullptr;
+  Options opt;
+};
+
+struct Stats {
+  int64_t levels = 0, partition_launches = 0, active_keys = 0, moved_keys = 0, equal_keys = 0;
+  int64_t small_segments = 0, small_keys = 0, local_segments = 0, local_keys = 0;
+  int64_t fallback_pivots = 0, kernel_launches = 0;
+  double partition_ms = 0, partition_bytes_per_key = 0;
+};
+
+// Implemented in bqs_api.cu.
+int fail_cuda(cudaError_t e, const char* what);
+void user_workspace(void** ptr, int64_t* bytes);
+void prepare_mempool();
+Ctrl* pinned_ctrl();
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();
+
+// Implemented in the per-dtype translation units.
+int run_i32(const Call& c, Stats& st);
+int run_i64(const Call& c, Stats& st);
+int run_f64(const Call& c, Stats& st);
+
+}  // namespace bqs

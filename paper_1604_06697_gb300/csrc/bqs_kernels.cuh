@@ -1,0 +1,626 @@
+// sm_103a kernels of the level-synchronous BlockQuicksort.
+//
+//   k_init_*      first work lists from the caller's array / segments
+//   k_pivot       pivot of every large segment (Sec. 2 / Sec. 4 pivot rules)
+//   k_partition   Algorithm 3 per tile: compare, buffer outcomes, rearrange
+//   k_bookkeep    children of every partitioned segment (Quicksort main loop)
+//   k_small_sort  sorting network for segments <= the small-segment cutoff
+//   k_fill        writes the class equal to a pivot into the final buffer
+#pragma once
+
+#include "bqs_common.cuh"
+
+namespace bqs {
+
+// ---- small helpers --------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+__device__ __forceinline__ int64_t isqrt64(int64_t n) {
+  int64_t r = (int64_t)sqrt((double)n);
+  while (r * r > n) --r;
+  while ((r + 1) * (r + 1) <= n) ++r;
+  return r;
+}
+
+// Warp-cooperative append of one child segment per lane (`active` lanes with len > 0)
+// to the lists of level q: the sorting network (len <= small_cutoff), the single-block
+// sort (len <= local_cutoff) or another partition level.  Every lane of the warp must
+// call it.  Slots come from one atomic per warp and list; a large segment's slot and
+// first tile come from one packed 64-bit atomic, so tile0 grows with the slot index.
+template <class KT>
+__device__ void route_warp(const Params& P, int q, bool active, int64_t off, int64_t len,
+                           int parity, int depth) {
+  Ctrl* c = P.ctrl;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = lanemask_lt();
+  const bool has = active && len > 0;
+  const bool small = has && len <= P.small_cutoff;
+  const bool local = has && !small && len <= P.local_cutoff;
+  const bool large = has && !small && !local;
+
+#pragma unroll
+  for (int kind = 0; kind < 2; ++kind) {
+    const bool mine = kind == 0 ? small : local;
+    const unsigned m = __ballot_sync(~0u, mine);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(kind == 0 ? &c->lists[q].small : &c->lists[q].local, (unsigned)__popc(m));
+    base = __shfl_sync(~0u, base, leader);
+    if (mine) {
+      const unsigned int slot = base + __popc(m & below);
+      if (slot < P.l.cap_run) {
+        Run r;
+        r.off = off; r.len = len; r.parity = parity; r.pad = 0;
+        (kind == 0 ? P.l.small[q] : P.l.local[q])[slot] = r;
+      } else {
+        atomicExch(&c->status, kStatusOverflow);
+      }
+    }
+  }
+
+  if (!__any_sync(~0u, large)) return;
+  const unsigned long long tiles = large ? (unsigned long long)((off + len - 1) / P.tile - off / P.tile + 1) : 0ull;
+  unsigned long long v = large ? (1ull | (tiles << 32)) : 0ull;
+  unsigned long long keys = large ? (unsigned long long)len : 0ull;
+  const unsigned long long own = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
+    const unsigned long long x = __shfl_up_sync(~0u, v, o);
+    if (lane >= o) v += x;
+    keys += __shfl_xor_sync(~0u, keys, o);
+  }
+  unsigned long long base = 0;
+  if (lane == 31) {
+    base = atomicAdd(&c->lists[q].large, v);
+    atomicAdd(&c->lists[q].large_keys, keys);
+  }
+  base = __shfl_sync(~0u, base, 31);
+  if (large) {
+    const unsigned long long old = base + v - own;   // exclusive prefix within the warp
+    const unsigned int slot = (unsigned int)old;
+    if (slot < P.l.cap_large) {
+      Seg s;
+      s.off = off; s.len = len; s.pkey = 0; s.pval = 0; s.depth = depth; s.parity = parity;
+      s.tile0 = (unsigned int)(old >> 32);
+      P.l.large[q][slot] = s;
+      P.l.cursor[q][slot] = 0ull;
+    } else {
+      atomicExch(&c->status, kStatusOverflow);
+    }
+  }
+}
+
+// ---- first work lists --------------------------------------------------------------------
+
+template <class KT>
+__global__ void k_init_single(Params P, int64_t n) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) route_warp<KT>(P, 0, threadIdx.x == 0, 0, n, 0, 0);
+}
+
+// A single segment with a caller-given pivot (bqs_partition): always partitioned.
+template <class KT>
+__global__ void k_init_partition(Params P, int64_t n, uint64_t pkey) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Seg s;
+    s.off = 0; s.len = n; s.pkey = pkey; s.pval = 0; s.depth = 0; s.parity = 0; s.tile0 = 0;
+    P.l.large[0][0] = s;
+    P.l.cursor[0][0] = 0ull;
+    P.ctrl->lists[0].large = 1ull | ((unsigned long long)((n - 1) / P.tile + 1) << 32);
+    P.ctrl->lists[0].large_keys = (unsigned long long)n;
+  }
+}
+
+// One thread per caller segment: check the offsets, then route the segment.
+template <class KT>
+__global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* __restrict__ offs,
+                                                       int64_t nseg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool ok = false;
+    int64_t a = 0, b = 0;
+    if (i < nseg) {
+      a = offs[i];
+      b = offs[i + 1];
+      ok = a >= 0 && b >= a;
+      if (!ok) atomicExch(&P.ctrl->status, kStatusInvalid);
+    }
+    route_warp<KT>(P, 0, ok, a, b - a, 0, 0);
+  }
+}
+
+// ---- shared-memory sorting network --------------------------------------------------------
+
+// Bitonic sort (Batcher) of m = power-of-two (ord key, payload) entries in shared
+// memory, ascending, by all threads of the block.  Ends with a barrier.
+template <bool PAIRS, class U>
+__device__ void block_bitonic_sort(U* k, uint32_t* v, int m) {
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < (m >> 1); i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        U a = k[lo], b = k[hi];
+        uint32_t va = 0, vb = 0;
+        if constexpr (PAIRS) { va = v[lo]; vb = v[hi]; }
+        const bool swap = up ? elem_less<PAIRS>(b, vb, a, va) : elem_less<PAIRS>(a, va, b, vb);
+        if (swap) {
+          k[lo] = b; k[hi] = a;
+          if constexpr (PAIRS) { v[lo] = vb; v[hi] = va; }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- pivot selection ---------------------------------------------------------------------
+
+template <class KT, bool PAIRS>
+struct Elem {
+  typename KT::U k;  // ord image
+  uint32_t v;
+};
+
+template <class KT, bool PAIRS>
+__device__ __forceinline__ Elem<KT, PAIRS> load_elem(const typename KT::U* keys,
+                                                     const uint32_t* vals, int64_t i) {
+  Elem<KT, PAIRS> e;
+  e.k = KT::ord(keys[i]);
+  e.v = PAIRS ? vals[i] : 0u;
+  return e;
+}
+
+template <class KT, bool PAIRS>
+__device__ __forceinline__ bool lt(const Elem<KT, PAIRS>& a, const Elem<KT, PAIRS>& b) {
+  return elem_less<PAIRS>(a.k, a.v, b.k, b.v);
+}
+
+// Median of three values (Sec. 2): the middle one of the ordered triple.
+template <class KT, bool PAIRS>
+__device__ Elem<KT, PAIRS> median3(Elem<KT, PAIRS> a, Elem<KT, PAIRS> b, Elem<KT, PAIRS> c) {
+  if (lt(b, a)) { auto t = a; a = b; b = t; }
+  if (lt(c, b)) { auto t = b; b = c; c = t; }
+  if (lt(b, a)) { auto t = a; a = b; b = t; }
+  return b;
+}
+
+// Median of five values.
+template <class KT, bool PAIRS>
+__device__ Elem<KT, PAIRS> median5(Elem<KT, PAIRS>* e) {
+  for (int i = 1; i < 5; ++i) {        // insertion sort of five
+    Elem<KT, PAIRS> x = e[i];
+    int j = i;
+    while (j > 0 && lt(x, e[j - 1])) { e[j] = e[j - 1]; --j; }
+    e[j] = x;
+  }
+  return e[2];
+}
+
+// One block per large segment: chooses the pivot and stores it in the descriptor.
+//  * median-of-3 of (first, middle, last) (Sec. 2);
+//  * sqrt rule (Sec. 4): below 64 keys median-of-3; below 20000 median-of-five-
+//    medians-of-five of 25 equally spaced keys; else the median of k = floor(sqrt(len))|1
+//    equally spaced keys (k capped at kMaxSample), sorted in shared memory;
+//  * a segment at the depth limit gets the midpoint of its ord-key range (payload
+//    range when all its keys are equal): each such level halves the range, so the
+//    recursion depth stays bounded by the key width (the role Heapsort plays in Sec. 2).
+// Block 0 also clears the counters of the lists this level is about to produce.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_pivot(Params P) {
+  using U = typename KT::U;
+  using E = Elem<KT, PAIRS>;
+  __shared__ U s_k[kMaxSample + 1];
+  __shared__ uint32_t s_v[PAIRS ? kMaxSample + 1 : 1];
+  __shared__ U s_red[2][8];
+  __shared__ uint32_t s_redv[2][8];
+
+  const int q = P.p ^ 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.ctrl->lists[q].large = 0; P.ctrl->lists[q].fill = 0; P.ctrl->lists[q].large_keys = 0;
+    P.ctrl->lists[q].small = 0; P.ctrl->lists[q].local = 0;
+  }
+  const unsigned int count = min((unsigned int)P.ctrl->lists[P.p].large, P.l.cap_large);
+  Seg* segs = P.l.large[P.p];
+  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
+    const Seg sg = segs[s];
+    const U* keys = (const U*)P.b.key[sg.parity];
+    const uint32_t* vals = P.b.val[sg.parity];
+    const int64_t b = sg.off, len = sg.len;
+    E piv;
+    if (sg.depth >= P.depth_limit) {
+      // Midpoint of the ord-key range (then of the payload range when it is empty).
+      U kmin = ~U(0), kmax = 0;
+      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        U k = KT::ord(keys[b + i]);
+        kmin = k < kmin ? k : kmin;
+        kmax = k > kmax ? k : kmax;
+      }
+      for (int o = 16; o; o >>= 1) {
+        U a = __shfl_xor_sync(~0u, kmin, o), c = __shfl_xor_sync(~0u, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = c > kmax ? c : kmax;
+      }
+      if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = kmin; s_red[1][threadIdx.x >> 5] = kmax; }
+      __syncthreads();
+      kmin = s_red[0][0]; kmax = s_red[1][0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        kmin = s_red[0][w] < kmin ? s_red[0][w] : kmin;
+        kmax = s_red[1][w] > kmax ? s_red[1][w] : kmax;
+      }
+      piv.k = kmin + (kmax - kmin) / 2;
+      piv.v = 0xFFFFFFFFu;  // keys == midpoint join the left side
+      if (PAIRS && kmin == kmax) {
+        uint32_t vmin = 0xFFFFFFFFu, vmax = 0;
+        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+          uint32_t v = vals[b + i];
+          vmin = min(vmin, v);
+          vmax = max(vmax, v);
+        }
+        for (int o = 16; o; o >>= 1) {
+          vmin = min(vmin, __shfl_xor_sync(~0u, vmin, o));
+          vmax = max(vmax, __shfl_xor_sync(~0u, vmax, o));
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { s_redv[0][threadIdx.x >> 5] = vmin; s_redv[1][threadIdx.x >> 5] = vmax; }
+        __syncthreads();
+        vmin = s_redv[0][0]; vmax = s_redv[1][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+          vmin = min(vmin, s_redv[0][w]);
+          vmax = max(vmax, s_redv[1][w]);
+        }
+        piv.v = vmin + (vmax - vmin) / 2;
+      }
+      if (threadIdx.x == 0) atomicAdd(&P.ctrl->fallbacks, 1ull);
+    } else if (P.pivot_rule == 0 || len < 64) {
+      if (threadIdx.x == 0)
+        piv = median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, b),
+                                 load_elem<KT, PAIRS>(keys, vals, b + len / 2),
+                                 load_elem<KT, PAIRS>(keys, vals, b + len - 1));
+    } else if (len < 20000) {
+      if (threadIdx.x == 0) {
+        E m[5];
+        for (int g = 0; g < 5; ++g) {
+          E e[5];
+          for (int j = 0; j < 5; ++j)
+            e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (5 * g + j) + 1) * len) / 50);
+          m[g] = median5<KT, PAIRS>(e);
+        }
+        piv = median5<KT, PAIRS>(m);
+      }
+    } else {
+      int64_t k = isqrt64(len) | 1;
+      if (k > kMaxSample) k = kMaxSample;
+      const int m = next_pow2((int)k);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (i < k) {
+          const int64_t pos = b + ((2 * (int64_t)i + 1) * len) / (2 * k);
+          s_k[i] = KT::ord(keys[pos]);
+          if constexpr (PAIRS) s_v[i] = vals[pos];
+        } else {
+          s_k[i] = ~U(0);
+          if constexpr (PAIRS) s_v[i] = 0xFFFFFFFFu;
+        }
+      }
+      block_bitonic_sort<PAIRS>(s_k, s_v, m);
+      if (threadIdx.x == 0) {
+        piv.k = s_k[(k - 1) / 2];
+        piv.v = PAIRS ? s_v[(k - 1) / 2] : 0u;
+      }
+    }
+    if (threadIdx.x == 0) {
+      segs[s].pkey = (uint64_t)KT::unord(piv.k);
+      segs[s].pval = piv.v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- the block partition step -----------------------------------------------------------
+
+// Algorithm 3, one tile per iteration.  A tile is THREADS*KPT consecutive keys of the
+// global index space (aligned to its size), clipped to one segment.
+//  scan phase:   every thread loads KPT keys with 16-byte loads and compares them with
+//                the pivot; the outcomes stay in registers (the offset buffers of Sec. 3).
+//  offsets:      per key round, a warp ballot gives the warp's "<" and ">" masks; their
+//                population counts give each key's rank in its warp and the warp's total;
+//                a scan over the warp totals gives tile offsets.
+//  reservation:  one 64-bit atomic on the segment's cursor reserves the tile's run of
+//                "<" keys (growing from the segment's start) and of ">" keys (growing
+//                from its end) at once.
+//  rearrange:    keys are staged in shared memory in output order and written out with
+//                consecutive threads on consecutive addresses.  Keys equal to the pivot
+//                are only counted; k_fill writes them.
+template <class KT, bool PAIRS, int THREADS, int KPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_partition(Params P) {
+  using U = typename KT::U;
+  constexpr int VEC = 16 / sizeof(U);
+  constexpr int NV = KPT / VEC;
+  constexpr int TILE = THREADS * KPT;
+  constexpr int WARPS = THREADS / 32;
+  static_assert(KPT % VEC == 0 && KPT <= 32 && TILE <= 32768, "tile shape");
+
+  __shared__ __align__(16) U s_key[TILE];
+  __shared__ __align__(16) uint32_t s_val[PAIRS ? TILE : 1];
+  __shared__ uint32_t s_wcnt[WARPS];            // (#<) | (#>) << 16 per warp
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_tseg[THREADS];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long lc = P.ctrl->lists[P.p].large;
+  const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
+  const Seg* __restrict__ segs = P.l.large[P.p];
+  unsigned long long* cursor = P.l.cursor[P.p];
+
+  for (uint32_t round = 0;; ++round) {
+    // Segment of each of this block's next THREADS tiles, one binary search per thread.
+    const uint64_t first = (uint64_t)blockIdx.x + (uint64_t)round * THREADS * gridDim.x;
+    if (first >= ntiles) break;
+    {
+      const uint64_t t = first + (uint64_t)threadIdx.x * gridDim.x;
+      if (t < ntiles) {
+        uint32_t lo = 0, hi = nseg;            // last segment with tile0 <= t
+        while (hi - lo > 1) {
+          uint32_t mid = (lo + hi) >> 1;
+          if (segs[mid].tile0 <= t) lo = mid; else hi = mid;
+        }
+        s_tseg[threadIdx.x] = lo;
+      }
+    }
+    __syncthreads();
+    for (int it = 0; it < THREADS; ++it) {
+      const uint64_t t = first + (uint64_t)it * gridDim.x;
+      if (t >= ntiles) break;
+      const uint32_t si = s_tseg[it];
+      const Seg sg = segs[si];
+      const U* __restrict__ src = (const U*)P.b.key[sg.parity];
+      U* __restrict__ dst = (U*)P.b.key[sg.parity ^ 1];
+      const uint32_t* __restrict__ vsrc = P.b.val[sg.parity];
+      uint32_t* __restrict__ vdst = P.b.val[sg.parity ^ 1];
+      const int64_t abase = (sg.off / TILE) * TILE + (int64_t)(t - sg.tile0) * TILE;
+      const int64_t lo = max(abase, sg.off), hi = min(abase + TILE, sg.off + sg.len);
+      const U pk = KT::ord((U)sg.pkey);
+      const uint32_t pv = sg.pval;
+
+      // Scan phase: load and compare.
+      U key[KPT];
+      uint32_t val[PAIRS ? KPT : 1];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int64_t i0 = abase + (int64_t)(j * THREADS + threadIdx.x) * VEC;
+        if (i0 >= lo && i0 + VEC <= hi) {
+          union { uint4 v; U e[VEC]; } u;
+          u.v = __ldcs(reinterpret_cast<const uint4*>(src + i0));
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) key[j * VEC + e] = u.e[e];
+          if constexpr (PAIRS) {
+            if constexpr (VEC == 4) {
+              uint4 w = __ldcs(reinterpret_cast<const uint4*>(vsrc + i0));
+              val[j * 4 + 0] = w.x; val[j * 4 + 1] = w.y; val[j * 4 + 2] = w.z; val[j * 4 + 3] = w.w;
+            } else {
+              uint2 w = __ldcs(reinterpret_cast<const uint2*>(vsrc + i0));
+              val[j * 2 + 0] = w.x; val[j * 2 + 1] = w.y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const int64_t i = i0 + e;
+            key[j * VEC + e] = (i >= lo && i < hi) ? src[i] : U(0);
+            if constexpr (PAIRS) val[j * VEC + e] = (i >= lo && i < hi) ? vsrc[i] : 0u;
+          }
+        }
+      }
+      uint32_t lt_bits = 0, gt_bits = 0;   // the thread's outcome buffer
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int64_t i0 = abase + (int64_t)(j * THREADS + threadIdx.x) * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const int r = j * VEC + e;
+          const bool valid = (i0 + e >= lo) && (i0 + e < hi);
+          const U k = KT::ord(key[r]);
+          const uint32_t v = PAIRS ? val[r] : 0u;
+          lt_bits |= (uint32_t)(valid && elem_less<PAIRS>(k, v, pk, pv)) << r;
+          gt_bits |= (uint32_t)(valid && elem_less<PAIRS>(pk, pv, k, v)) << r;
+        }
+      }
+
+      // Offsets: warp totals from ballots, then a scan over the warps.
+      uint32_t wlt = 0, wgt = 0;
+#pragma unroll
+      for (int r = 0; r < KPT; ++r) {
+        wlt += __popc(__ballot_sync(~0u, (lt_bits >> r) & 1));
+        wgt += __popc(__ballot_sync(~0u, (gt_bits >> r) & 1));
+      }
+      if (lane == 0) s_wcnt[warp] = wlt | (wgt << 16);
+      __syncthreads();
+      uint32_t off_lt = 0, off_gt = 0, nlt = 0, ngt = 0;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_wcnt[w];
+        if (w < warp) { off_lt += c & 0xFFFF; off_gt += c >> 16; }
+        nlt += c & 0xFFFF;
+        ngt += c >> 16;
+      }
+      if (threadIdx.x == 0)   // reservation: one atomic per tile
+        s_base = atomicAdd(&cursor[si], (unsigned long long)nlt | ((unsigned long long)ngt << 32));
+
+      // Stage in output order: "<" keys at [0, nlt), ">" keys at [nlt, nlt+ngt).
+      const unsigned below = lanemask_lt();
+      uint32_t run_lt = off_lt, run_gt = nlt + off_gt;
+#pragma unroll
+      for (int r = 0; r < KPT; ++r) {
+        const unsigned mlt = __ballot_sync(~0u, (lt_bits >> r) & 1);
+        const unsigned mgt = __ballot_sync(~0u, (gt_bits >> r) & 1);
+        if ((lt_bits >> r) & 1) {
+          const uint32_t pos = run_lt + __popc(mlt & below);
+          s_key[pos] = key[r];
+          if constexpr (PAIRS) s_val[pos] = val[r];
+        }
+        if ((gt_bits >> r) & 1) {
+          const uint32_t pos = run_gt + __popc(mgt & below);
+          s_key[pos] = key[r];
+          if constexpr (PAIRS) s_val[pos] = val[r];
+        }
+        run_lt += __popc(mlt);
+        run_gt += __popc(mgt);
+      }
+      __syncthreads();
+
+      // Rearrangement: coalesced write-out of the two runs.
+      const unsigned long long base = s_base;
+      const int64_t left = sg.off + (int64_t)(uint32_t)base;
+      const int64_t right = sg.off + sg.len - (int64_t)(uint32_t)(base >> 32) - ngt;
+      const uint32_t nout = nlt + ngt;
+      for (uint32_t i = threadIdx.x; i < nout; i += THREADS) {
+        const int64_t g = i < nlt ? left + i : right + (i - nlt);
+        dst[g] = s_key[i];
+        if constexpr (PAIRS) vdst[g] = s_val[i];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---- children of the partitioned segments ------------------------------------------------
+
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_bookkeep(Params P) {
+  const int p = P.p, q = p ^ 1;
+  const int lane = threadIdx.x & 31;
+  const unsigned int count = min((unsigned int)P.ctrl->lists[p].large, P.l.cap_large);
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const unsigned int s = base + threadIdx.x;
+    const bool active = s < count;
+    Seg sg{};
+    int64_t nlt = 0, ngt = 0, neq = 0;
+    if (active) {
+      sg = P.l.large[p][s];
+      const unsigned long long cur = P.l.cursor[p][s];
+      nlt = (uint32_t)cur;
+      ngt = (uint32_t)(cur >> 32);
+      neq = sg.len - nlt - ngt;
+    }
+    // Statistics, one atomic per warp.
+    unsigned long long moved = (unsigned long long)(nlt + ngt), eq = (unsigned long long)neq;
+    for (int o = 16; o; o >>= 1) {
+      moved += __shfl_xor_sync(~0u, moved, o);
+      eq += __shfl_xor_sync(~0u, eq, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&P.ctrl->moved_keys, moved);
+      atomicAdd(&P.ctrl->equal_keys, eq);
+    }
+    // The keys equal to the pivot are final: queue them for k_fill (packed atomic).
+    const bool fills = active && neq > 0;
+    if (__any_sync(~0u, fills)) {
+      const unsigned long long ftiles = fills ? (unsigned long long)((neq + kFillTile - 1) / kFillTile) : 0ull;
+      unsigned long long v = fills ? (1ull | (ftiles << 32)) : 0ull;
+      const unsigned long long own = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long x = __shfl_up_sync(~0u, v, o);
+        if (lane >= o) v += x;
+      }
+      unsigned long long fb = 0;
+      if (lane == 31) fb = atomicAdd(&P.ctrl->lists[p].fill, v);
+      fb = __shfl_sync(~0u, fb, 31);
+      if (fills) {
+        const unsigned long long old = fb + v - own;
+        const unsigned int slot = (unsigned int)old;
+        if (slot < P.l.cap_fill) {
+          Fill f;
+          f.off = sg.off + nlt; f.len = neq; f.pkey = sg.pkey; f.pval = sg.pval;
+          f.tile0 = (unsigned int)(old >> 32);
+          P.l.fill[p][slot] = f;
+        } else {
+          atomicExch(&P.ctrl->status, kStatusOverflow);
+        }
+      }
+    }
+    if (P.route_children) {   // both sides exclude the pivot class (Sec. 2)
+      route_warp<KT>(P, q, active, sg.off, nlt, sg.parity ^ 1, sg.depth + 1);
+      route_warp<KT>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
+    }
+  }
+}
+
+// ---- small-segment sort ----------------------------------------------------------------
+
+// One block per segment of at most kMaxSmall keys: load into shared memory (padded
+// with the largest order key), bitonic sort, write into the final buffer.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_small_sort(Params P, int p) {
+  using U = typename KT::U;
+  __shared__ __align__(16) U s_k[kMaxSmall];
+  __shared__ __align__(16) uint32_t s_v[PAIRS ? kMaxSmall : 1];
+  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  const Run* runs = P.l.small[p];
+  U* fk = (U*)P.b.final_key;
+  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
+    const Run r = runs[s];
+    const U* src = (const U*)P.b.key[r.parity];
+    const uint32_t* vsrc = P.b.val[r.parity];
+    const int len = (int)r.len;
+    const int m = next_pow2(len < 2 ? 2 : len);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      s_k[i] = i < len ? KT::ord(src[r.off + i]) : ~U(0);
+      if constexpr (PAIRS) s_v[i] = i < len ? vsrc[r.off + i] : 0xFFFFFFFFu;
+    }
+    block_bitonic_sort<PAIRS>(s_k, s_v, m);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      fk[r.off + i] = KT::unord(s_k[i]);
+      if constexpr (PAIRS) P.b.final_val[r.off + i] = s_v[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- keys equal to a pivot ----------------------------------------------------------------
+
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_fill(Params P, int p) {
+  using U = typename KT::U;
+  __shared__ uint32_t s_f;
+  const unsigned long long lc = P.ctrl->lists[p].fill;
+  const uint32_t count = min((uint32_t)lc, P.l.cap_fill), tiles = (uint32_t)(lc >> 32);
+  const Fill* fills = P.l.fill[p];
+  if (count == 0) return;
+  U* fk = (U*)P.b.final_key;
+  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      uint32_t lo = 0, hi = count;
+      while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (fills[mid].tile0 <= t) lo = mid; else hi = mid;
+      }
+      s_f = lo;
+    }
+    __syncthreads();
+    const Fill f = fills[s_f];
+    const int64_t b = f.off + (int64_t)(t - f.tile0) * kFillTile;
+    const int64_t e = min(b + kFillTile, f.off + f.len);
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      fk[i] = (U)f.pkey;
+      if constexpr (PAIRS) P.b.final_val[i] = f.pval;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace bqs

@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Sorted outputs are unique, so the comparison is bit-exact (tolerance 0;
+float64 compared by bits).  Partitions are compared on what is unique: the
+split and the multiset of each side.  Sizes span several tiles and ragged
+tails; edge cases cover empty, single-key, all-equal and tile-boundary sizes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06697_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["int32", "int64", "float64"]
+EDGE_SIZES = [0, 1, 2, 3, 4, 15, 16, 17, 31, 33, 127, 128, 129, 255, 257, 2047, 2048, 2049,
+              4095, 4096, 4097, 8191, 8193, 65535, 65537, (1 << 20) + 1]
+
+
+@pytest.fixture(scope="module")
+def bqs():
+    import torch
+    from paper_1604_06697_gb300 import build
+    build.build()
+    import paper_1604_06697_gb300 as m
+    torch.cuda.init()
+    return m
+
+
+@pytest.fixture(autouse=True)
+def default_options(bqs):
+    saved = {k: bqs.get_option(k) for k in bqs.OPTIONS}
+    yield
+    for k, v in saved.items():
+        bqs.set_option(k, v)
+
+
+def gpu_sort(bqs, a):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    bqs.sort(t)
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def assert_same_bits(got, want):
+    assert got.dtype == want.dtype and got.shape == want.shape
+    gu = got.view(np.uint32 if got.itemsize == 4 else np.uint64)
+    wu = want.view(np.uint32 if want.itemsize == 4 else np.uint64)
+    if not np.array_equal(gu, wu):
+        idx = np.nonzero(gu != wu)[0]
+        raise AssertionError(f"{idx.size} mismatches, first at {idx[:5]}: got {got[idx[:5]]} "
+                             f"want {want[idx[:5]]}")
+
+
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sort_matches_oracle_edge_sizes(bqs, dtype, dist):
+    for n in EDGE_SIZES:
+        a = inputs.make_keys(n, dtype, dist, seed=n + 1)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+
+
+@pytest.mark.parametrize("pivot", [0, 1])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sort_pivot_rules_and_tiles(bqs, dtype, tile, pivot):
+    bqs.set_option("pivot", pivot)
+    bqs.set_option("tile", tile)
+    for n, dist in [(100_000, "uniform"), (300_001, "mod_sqrt"), (1 << 18, "swapped_1pct"),
+                    (70_001, "reversed")]:
+        a = inputs.make_keys(n, dtype, dist, seed=3)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
+
+
+@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 1000, 2048])
+def test_small_cutoffs(bqs, cutoff):
+    bqs.set_option("small_cutoff", cutoff)
+    for dtype in DTYPES:
+        for n in (5, 100, 3000, 50_001):
+            a = inputs.make_keys(n, dtype, "uniform", seed=n)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+
+
+def test_float64_special_values(bqs):
+    vals = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, 5e-324, -5e-324, 2.5, -2.5,
+                     np.finfo(np.float64).max, -np.finfo(np.float64).max] * 500)
+    perm = np.argsort(inputs.splitmix64(1, vals.size))
+    a = vals[perm]
+    for cutoff in (2, 64, 2048):
+        bqs.set_option("small_cutoff", cutoff)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+
+
+@pytest.mark.parametrize("limit", [0, 1, 3])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_depth_limit_fallback(bqs, dtype, limit):
+    # Past the depth limit every segment is split at the midpoint of its key range.
+    bqs.set_option("depth_limit", limit)
+    bqs.set_option("small_cutoff", 16)
+    for dist in ("uniform", "mod_sqrt", "all_equal", "sorted"):
+        a = inputs.make_keys(200_001, dtype, dist, seed=limit)
+        got = gpu_sort(bqs, a)
+        assert_same_bits(got, oracle.sort(a))
+    assert bqs.stats()["fallback_pivots"] > 0 or dist == "all_equal"
+
+
+def test_extreme_int_values(bqs):
+    for dtype in ("int32", "int64"):
+        info = np.iinfo(dtype)
+        a = np.array([info.max, info.min, 0, -1, 1, info.max, info.min] * 3001, dtype=dtype)
+        a = a[np.argsort(inputs.splitmix64(2, a.size))]
+        for cutoff in (2, 2048):
+            bqs.set_option("small_cutoff", cutoff)
+            bqs.set_option("depth_limit", 0 if cutoff == 2 else -1)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+
+
+# ---- key-value pairs --------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sort_pairs_matches_oracle(bqs, dtype):
+    import torch
+    for n in (0, 1, 2, 17, 2049, 100_003, 1 << 20):
+        keys = (inputs.splitmix64(5, n) % np.uint64(max(1, n // 50 + 1))).astype(dtype)
+        vals = np.arange(n, dtype=np.uint32)[np.argsort(inputs.splitmix64(6, n))].astype(np.uint32)
+        tk = torch.from_numpy(keys).cuda()
+        tv = torch.from_numpy(vals.view(np.int32)).cuda()
+        bqs.sort_pairs(tk, tv)
+        wk, wv = oracle.sort_pairs(keys, vals)
+        assert_same_bits(tk.cpu().numpy(), wk)
+        assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
+
+
+def test_sort_pairs_workload_shape_with_fallback(bqs):
+    import torch
+    keys, vals = inputs.make_pairs(1 << 18, seed=1)
+    for limit in (-1, 2):
+        bqs.set_option("depth_limit", limit)
+        tk, tv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+        bqs.sort_pairs(tk, tv)
+        wk, wv = oracle.sort_pairs(keys, vals)
+        assert_same_bits(tk.cpu().numpy(), wk)
+        assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
+
+
+# ---- partition ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_partition_split_and_sides(bqs, dtype):
+    import torch
+    for n in (1, 2, 100, 4096, 4097, 100_001, 1 << 20):
+        a = (inputs.splitmix64(n, n) % np.uint64(1000)).astype(dtype)
+        for pivot in (-5, 0, 500, 999, 1000):
+            out, split = bqs.partition(torch.from_numpy(a).cuda(), pivot)
+            got = out.cpu().numpy()
+            want, wsplit = oracle.partition_by_value(a, pivot)
+            assert split == wsplit
+            assert_same_bits(np.sort(got[:split]), np.sort(want[:wsplit]))
+            assert_same_bits(np.sort(got[split:]), np.sort(want[wsplit:]))
+            # keys equal to the pivot come first on the right side
+            neq = int(np.count_nonzero(a == pivot))
+            assert np.all(got[split:split + neq] == pivot)
+
+
+def test_partition_rejects_overlap(bqs):
+    import torch
+    t = torch.arange(1000, dtype=torch.int32, device="cuda")
+    with pytest.raises(bqs.BqsError):
+        bqs.partition(t, 5, out=t)
+
+
+# ---- segmented ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_segmented_matches_oracle(bqs, dtype):
+    import torch
+    lens = [0, 1, 0, 2, 5000, 17, 0, 2048, 2049, 1, 300_000, 3, 65536, 0]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    a = inputs.make_keys(int(off[-1]), dtype, "uniform", seed=4)
+    t = torch.from_numpy(a).cuda()
+    bqs.sort_segmented(t, torch.from_numpy(off).cuda())
+    assert_same_bits(t.cpu().numpy(), oracle.sort_segmented(a, off))
+
+
+def test_segmented_log_uniform_batch(bqs):
+    import torch
+    keys, off = inputs.make_segments(4096, seed=2, lo=16, hi=65536)
+    t = torch.from_numpy(keys).cuda()
+    bqs.sort_segmented(t, torch.from_numpy(off).cuda())
+    assert_same_bits(t.cpu().numpy(), oracle.sort_segmented(keys, off))
+
+
+def test_segmented_rejects_decreasing_offsets(bqs):
+    import torch
+    t = torch.zeros(100, dtype=torch.int32, device="cuda")
+    off = torch.tensor([0, 50, 40, 100], dtype=torch.int64, device="cuda")
+    with pytest.raises(bqs.BqsError):
+        bqs.sort_segmented(t, off)
+
+
+# ---- larger sizes -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sort_2pow24_matches_oracle(bqs, dtype, dist):
+    bqs.set_option("pivot", 1)
+    a = inputs.make_keys(1 << 24, dtype, dist, seed=1)
+    assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt"))
+
+
+def test_sort_config1_median_of_3(bqs):
+    # 2^20 int32 keys uniform over the full range from seed 0, median-of-3 pivots.
+    bqs.set_option("pivot", 0)
+    a = inputs.make_keys(1 << 20, "int32", "uniform", seed=0)
+    assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="mo3"))
