@@ -194,7 +194,7 @@ int bqs_set_option(int32_t opt, int64_t value) {
       g_opt.timing = value;
       return BQS_OK;
     case BQS_OPT_TILE:
-      if (value < 0 || value > 3) return BQS_ERR_INVALID;
+      if (value < 0 || value > 3) return BQS_ERR_INVALID;  // the four variants() entries
       g_opt.tile_variant = value;
       return BQS_OK;
     case BQS_OPT_LOCAL_CUTOFF:

@@ -91,6 +91,8 @@ struct ListCounts {
   unsigned long long fill;
   unsigned long long large_keys;  // sum of the large segments' lengths
   unsigned int small;
+  unsigned int tiny;    // small segments of at most kWarpSortMax keys
+  unsigned int pad_;
   unsigned int local;
 };
 
@@ -118,6 +120,7 @@ struct Lists {
   Seg* large[2];
   unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
   Run* small[2];
+  Run* tiny[2];
   Run* local[2];
   Fill* fill[2];
   uint32_t cap_large, cap_run, cap_fill;
@@ -135,14 +138,18 @@ struct Params {
   int route_children; // 0: a single partition step (no recursion)
   int tile;           // keys per partition tile (for tile counts)
   int pad;
+  int64_t n_keys;     // length of the key arrays
 };
 
 // Device status codes (mirrors the public bqs_status values).
 constexpr int kStatusInvalid = -1;
+constexpr int kStatusTimeout = -4;   // a bounded device-side wait gave up
 constexpr int kStatusOverflow = -6;  // an internal list overflowed its capacity
 
 constexpr int kFillTile = 8192;      // keys per fill task
 constexpr int kMaxSmall = 2048;      // largest small-segment cutoff
-constexpr int kMaxSample = 2047;     // largest pivot sample
+constexpr int kWarpSortMax = 256;    // small segments up to this length are sorted by one warp
+constexpr int kMaxSample = 511;      // largest pivot sample
+constexpr int kInlineFill = 32;      // pivot-class runs up to this length are written inline
 
 }  // namespace bqs

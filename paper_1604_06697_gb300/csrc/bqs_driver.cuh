@@ -14,6 +14,8 @@
 
 #include "bqs_internal.h"
 #include "bqs_kernels.cuh"
+#include "bqs_small.cuh"
+#include "bqs_tma.cuh"
 
 namespace bqs {
 
@@ -21,7 +23,7 @@ namespace bqs {
 
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
-  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
+  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -50,6 +52,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.large[i] = take((size_t)L.cap_large * sizeof(Seg));
     L.cursor[i] = take((size_t)L.cap_large * 8);
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.tiny[i] = take((size_t)L.cap_run * sizeof(Run));
     L.local[i] = take((size_t)L.cap_run * sizeof(Run));
     L.fill[i] = take((size_t)L.cap_fill * sizeof(Fill));
   }
@@ -95,6 +98,7 @@ inline int acquire_scratch(Scratch& s, size_t bytes, cudaStream_t st) {
 struct Variant {
   int threads, kpt;
   const void* fn;
+  size_t smem;        // dynamic shared memory per block
   void (*launch)(const Params&, int grid, cudaStream_t);
 };
 
@@ -105,25 +109,40 @@ void launch_partition(const Params& P, int grid, cudaStream_t st) {
 
 template <class KT, bool PAIRS, int T, int K, int MINB>
 Variant make_variant() {
-  return Variant{T, K, (const void*)k_partition<KT, PAIRS, T, K, MINB>,
+  return Variant{T, K, (const void*)k_partition<KT, PAIRS, T, K, MINB>, 0,
                  &launch_partition<KT, PAIRS, T, K, MINB>};
 }
 
+template <class KT, bool PAIRS, int T, int K, int STAGES>
+void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
+  k_partition_tma<KT, PAIRS, T, K, STAGES>
+      <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES>::smem, st>>>(P);
+}
+
+template <class KT, bool PAIRS, int T, int K, int STAGES>
+Variant make_tma_variant() {
+  const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES>;
+  const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES>::smem;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES>};
+}
+
 // Tile shapes offered to the autotuner: keys per tile = threads * keys-per-thread.
+// 0-2: TMA-fed persistent kernels; 3: the register-loading kernel.
 template <class KT, bool PAIRS>
 const std::vector<Variant>& variants() {
   static const std::vector<Variant> v = [] {
     std::vector<Variant> r;
     if constexpr (sizeof(typename KT::U) == 4) {
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 3>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 32, 2>());
+      r.push_back(make_tma_variant<KT, PAIRS, 512, 16, 2>());
       r.push_back(make_variant<KT, PAIRS, 256, 16, 4>());
-      r.push_back(make_variant<KT, PAIRS, 256, 32, 2>());
-      r.push_back(make_variant<KT, PAIRS, 512, 16, 2>());
-      r.push_back(make_variant<KT, PAIRS, 128, 32, 4>());
     } else {
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 3>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 2>());
+      r.push_back(make_tma_variant<KT, PAIRS, 512, 8, 2>());
       r.push_back(make_variant<KT, PAIRS, 256, 8, 4>());
-      r.push_back(make_variant<KT, PAIRS, 256, 16, 2>());
-      r.push_back(make_variant<KT, PAIRS, 512, 8, 2>());
-      r.push_back(make_variant<KT, PAIRS, 128, 16, 4>());
     }
     return r;
   }();
@@ -131,7 +150,7 @@ const std::vector<Variant>& variants() {
 }
 
 // Persistent grid of a kernel: resident blocks per SM times the SM count.
-inline int persistent_grid(const void* fn, int threads) {
+inline int persistent_grid(const void* fn, int threads, size_t smem) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, int>> cache;
   int dev = 0;
@@ -141,7 +160,7 @@ inline int persistent_grid(const void* fn, int threads) {
     if (e.first == fn) return e.second;
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   const int g_ = std::max(1, sms * std::max(1, per));
   cache.emplace_back(fn, g_);
   return g_;
@@ -158,6 +177,12 @@ inline int sm_count() {
 }
 
 // ---- the level loop --------------------------------------------------------------------------
+
+inline int status_code(int device_status) {
+  if (device_status == kStatusInvalid) return kErrInvalid;
+  if (device_status == kStatusTimeout) return kErrTimeout;
+  return kErrInternal;
+}
 
 #define BQS_CK(call)                                              \
   do {                                                            \
@@ -197,6 +222,7 @@ int run_call(const Call& c, Stats& st) {
     P.l.large[i] = (Seg*)(w + L.large[i]);
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
+    P.l.tiny[i] = (Run*)(w + L.tiny[i]);
     P.l.local[i] = (Run*)(w + L.local[i]);
     P.l.fill[i] = (Fill*)(w + L.fill[i]);
   }
@@ -206,6 +232,7 @@ int run_call(const Call& c, Stats& st) {
   P.local_cutoff = local_cutoff;
   P.route_children = c.partition_only ? 0 : 1;
   P.tile = tile;
+  P.n_keys = c.n;
   {
     int64_t top = c.n;  // depth limit 2*floor(log2 n)+3 of the largest array (Sec. 2)
     int lg = 0;
@@ -229,12 +256,13 @@ int run_call(const Call& c, Stats& st) {
     BQS_CK(cudaGetLastError());
     BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     BQS_CK(cudaStreamSynchronize(s));
-    if (host->status) return host->status == kStatusInvalid ? kErrInvalid : kErrInternal;
+    if (host->status) return status_code(host->status);
     cur = host->lists[0];
   } else {
     k_init_single<KT><<<1, 32, 0, s>>>(P, c.n);
     st.kernel_launches += 1;
-    if (c.n <= small_cutoff) cur.small = 1;
+    if (c.n <= small_cutoff && c.n <= kWarpSortMax) cur.tiny = 1;
+    else if (c.n <= small_cutoff) cur.small = 1;
     else if (c.n <= local_cutoff) cur.local = 1;
     else {
       cur.large = 1ull | ((unsigned long long)((c.n - 1) / tile + 1) << 32);
@@ -244,7 +272,7 @@ int run_call(const Call& c, Stats& st) {
   BQS_CK(cudaGetLastError());
 
   const int sms = sm_count();
-  const int part_grid_max = persistent_grid(var.fn, var.threads);
+  const int part_grid_max = persistent_grid(var.fn, var.threads, var.smem);
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
   size_t ev_used = 0;
 
@@ -281,16 +309,21 @@ int run_call(const Call& c, Stats& st) {
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 3;
     }
+    if (cur.tiny) {
+      st.small_segments += cur.tiny;
+      k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s>>>(P, P.p);
+      st.kernel_launches += 1;
+    }
     if (cur.small) {
       st.small_segments += cur.small;
-      k_small_sort<KT, PAIRS><<<(int)std::min<uint32_t>(cur.small, 16 * sms), 256, 0, s>>>(P, P.p);
+      k_small_block<KT, PAIRS><<<(int)std::min<uint32_t>(cur.small, 16 * sms), 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
     BQS_CK(cudaGetLastError());
     if (!nlarge) break;
     BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     BQS_CK(cudaStreamSynchronize(s));
-    if (host->status) return host->status == kStatusInvalid ? kErrInvalid : kErrInternal;
+    if (host->status) return status_code(host->status);
     if (c.partition_only) {
       // split = #(< pivot); the cursor of the single segment holds it.
       unsigned long long cursor = 0;

@@ -45,25 +45,29 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
   const int lane = threadIdx.x & 31;
   const unsigned below = lanemask_lt();
   const bool has = active && len > 0;
-  const bool small = has && len <= P.small_cutoff;
-  const bool local = has && !small && len <= P.local_cutoff;
-  const bool large = has && !small && !local;
+  const bool sorted_now = has && len <= P.small_cutoff;
+  const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
+  const bool small = sorted_now && !tiny;                // one block per segment
+  const bool local = has && !sorted_now && len <= P.local_cutoff;
+  const bool large = has && !sorted_now && !local;
 
 #pragma unroll
-  for (int kind = 0; kind < 2; ++kind) {
-    const bool mine = kind == 0 ? small : local;
+  for (int kind = 0; kind < 3; ++kind) {
+    const bool mine = kind == 0 ? tiny : kind == 1 ? small : local;
     const unsigned m = __ballot_sync(~0u, mine);
     if (!m) continue;
     const int leader = __ffs(m) - 1;
+    unsigned int* counter = kind == 0 ? &c->lists[q].tiny : kind == 1 ? &c->lists[q].small : &c->lists[q].local;
+    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : P.l.local[q];
     unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(kind == 0 ? &c->lists[q].small : &c->lists[q].local, (unsigned)__popc(m));
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
     base = __shfl_sync(~0u, base, leader);
     if (mine) {
       const unsigned int slot = base + __popc(m & below);
       if (slot < P.l.cap_run) {
         Run r;
         r.off = off; r.len = len; r.parity = parity; r.pad = 0;
-        (kind == 0 ? P.l.small[q] : P.l.local[q])[slot] = r;
+        list[slot] = r;
       } else {
         atomicExch(&c->status, kStatusOverflow);
       }
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   const int q = P.p ^ 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.ctrl->lists[q].large = 0; P.ctrl->lists[q].fill = 0; P.ctrl->lists[q].large_keys = 0;
-    P.ctrl->lists[q].small = 0; P.ctrl->lists[q].local = 0;
+    P.ctrl->lists[q].small = 0; P.ctrl->lists[q].local = 0; P.ctrl->lists[q].tiny = 0;
   }
   const unsigned int count = min((unsigned int)P.ctrl->lists[P.p].large, P.l.cap_large);
   Seg* segs = P.l.large[P.p];
@@ -527,8 +531,17 @@ __global__ void __launch_bounds__(256) k_bookkeep(Params P) {
       atomicAdd(&P.ctrl->moved_keys, moved);
       atomicAdd(&P.ctrl->equal_keys, eq);
     }
-    // The keys equal to the pivot are final: queue them for k_fill (packed atomic).
-    const bool fills = active && neq > 0;
+    // The keys equal to the pivot are final.  A short run is written here; longer runs
+    // are queued for k_fill (packed atomic).
+    if (active && neq > 0 && neq <= kInlineFill) {
+      using U = typename KT::U;
+      U* fk = (U*)P.b.final_key + sg.off + nlt;
+      for (int64_t j = 0; j < neq; ++j) {
+        fk[j] = (U)sg.pkey;
+        if constexpr (PAIRS) P.b.final_val[sg.off + nlt + j] = sg.pval;
+      }
+    }
+    const bool fills = active && neq > kInlineFill;
     if (__any_sync(~0u, fills)) {
       const unsigned long long ftiles = fills ? (unsigned long long)((neq + kFillTile - 1) / kFillTile) : 0ull;
       unsigned long long v = fills ? (1ull | (ftiles << 32)) : 0ull;
