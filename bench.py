@@ -65,11 +65,21 @@ def measured_peak_gbs():
 
 
 def committed_traffic():
-    """DRAM bytes per processed key of the partition kernel from the committed ncu summary."""
+    """DRAM bytes per processed key of the partition kernel from the committed ncu summary.
+
+    Returns None when the kernel's source files changed since the capture (their
+    hash is stored beside the counters), so a stale figure is never reported.
+    """
+    import hashlib
     path = os.path.join(ROOT, "profiles", "partition_traffic.json")
     try:
         with open(path) as f:
-            return json.load(f)
+            tr = json.load(f)
+        h = hashlib.sha256()
+        for rel in tr["source_files"]:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        return tr if h.hexdigest()[:16] == tr["source_sha256_16"] else None
     except Exception:
         return None
 

@@ -198,7 +198,7 @@ int bqs_set_option(int32_t opt, int64_t value) {
       g_opt.tile_variant = value;
       return BQS_OK;
     case BQS_OPT_LOCAL_CUTOFF:
-      if (value < 0 || value > (1 << 20)) return BQS_ERR_INVALID;
+      if (value < -1 || value > (1 << 20)) return BQS_ERR_INVALID;
       g_opt.local_cutoff = value;
       return BQS_OK;
     default:

@@ -92,7 +92,7 @@ struct ListCounts {
   unsigned long long large_keys;  // sum of the large segments' lengths
   unsigned int small;
   unsigned int tiny;    // small segments of at most kWarpSortMax keys
-  unsigned int pad_;
+  unsigned int todo;    // large segments whose pivot k_pivot chooses
   unsigned int local;
 };
 
@@ -121,6 +121,7 @@ struct Lists {
   unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
   Run* small[2];
   Run* tiny[2];
+  uint32_t* todo[2];              // slots of large segments waiting for k_pivot
   Run* local[2];
   Fill* fill[2];
   uint32_t cap_large, cap_run, cap_fill;
@@ -140,6 +141,14 @@ struct Params {
   int pad;
   int64_t n_keys;     // length of the key arrays
 };
+
+// Tiles of a segment start at its first key rounded down to a 16-byte group (4 keys):
+// tile k covers [tile_origin(off) + k*tile, + tile) clipped to the segment, so only the
+// first tile can start before the segment and only the last one can end early.
+__host__ __device__ __forceinline__ int64_t tile_origin(int64_t off) { return off & ~(int64_t)3; }
+__host__ __device__ __forceinline__ int64_t tile_count(int64_t off, int64_t len, int tile) {
+  return (off + len - tile_origin(off) + tile - 1) / tile;
+}
 
 // Device status codes (mirrors the public bqs_status values).
 constexpr int kStatusInvalid = -1;

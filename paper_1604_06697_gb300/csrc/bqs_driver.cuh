@@ -14,6 +14,7 @@
 
 #include "bqs_internal.h"
 #include "bqs_kernels.cuh"
+#include "bqs_local.cuh"
 #include "bqs_small.cuh"
 #include "bqs_tma.cuh"
 
@@ -23,7 +24,7 @@ namespace bqs {
 
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
-  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
+  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -53,6 +54,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.cursor[i] = take((size_t)L.cap_large * 8);
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
     L.tiny[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.todo[i] = take((size_t)L.cap_large * sizeof(uint32_t));
     L.local[i] = take((size_t)L.cap_run * sizeof(Run));
     L.fill[i] = take((size_t)L.cap_fill * sizeof(Fill));
   }
@@ -149,6 +151,28 @@ const std::vector<Variant>& variants() {
   return v;
 }
 
+// Shape of the single-block local sort: keys per block (L) and threads; both ping-pong
+// buffers of L keys (+ payloads) fit in shared memory.
+template <class KT, bool PAIRS>
+struct LocalCap {
+  static constexpr int L = PAIRS ? 8192 : (int)(65536 / sizeof(typename KT::U));
+  static constexpr int T = 512;
+  static constexpr size_t smem = LocalShape<KT, PAIRS, L>::smem;
+  static const void* fn() {
+    static const void* f = [] {
+      const void* k = (const void*)k_local_sort<KT, PAIRS, L, T>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return k;
+    }();
+    return f;
+  }
+  static int grid();
+  static void launch(const Params& P, int p, int grid, cudaStream_t st) {
+    fn();
+    k_local_sort<KT, PAIRS, L, T><<<grid, T, smem, st>>>(P, p);
+  }
+};
+
 // Persistent grid of a kernel: resident blocks per SM times the SM count.
 inline int persistent_grid(const void* fn, int threads, size_t smem) {
   static std::mutex mu;
@@ -176,6 +200,11 @@ inline int sm_count() {
   return sms;
 }
 
+template <class KT, bool PAIRS>
+int LocalCap<KT, PAIRS>::grid() {
+  return persistent_grid(fn(), T, smem);
+}
+
 // ---- the level loop --------------------------------------------------------------------------
 
 inline int status_code(int device_status) {
@@ -198,9 +227,13 @@ int run_call(const Call& c, Stats& st) {
   const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
   const int tile = var.threads * var.kpt;
   const int small_cutoff = c.partition_only ? 1 : (int)c.opt.small_cutoff;
-  // Segments up to local_cutoff would be finished by one thread block; until that kernel
-  // exists every segment above the small cutoff is partitioned.
-  const int local_cutoff = small_cutoff;
+  // Segments up to local_cutoff keys are finished by one thread block in shared memory.
+  constexpr int kLocalL = LocalCap<KT, PAIRS>::L;
+  const int local_cutoff =
+      c.partition_only ? 1
+                       : std::max(small_cutoff, c.opt.local_cutoff < 0
+                                                    ? kLocalL
+                                                    : (int)std::min<int64_t>(c.opt.local_cutoff, kLocalL));
 
   const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only);
   Scratch scratch;
@@ -223,6 +256,7 @@ int run_call(const Call& c, Stats& st) {
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
     P.l.tiny[i] = (Run*)(w + L.tiny[i]);
+    P.l.todo[i] = (uint32_t*)(w + L.todo[i]);
     P.l.local[i] = (Run*)(w + L.local[i]);
     P.l.fill[i] = (Fill*)(w + L.fill[i]);
   }
@@ -251,7 +285,7 @@ int run_call(const Call& c, Stats& st) {
     cur.large_keys = (unsigned long long)c.n;
   } else if (c.seg_offsets) {
     const int g = (int)std::min<int64_t>((c.nseg + 255) / 256, 4 * sm_count());
-    k_init_segments<KT><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
+    k_init_segments<KT, PAIRS><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
     st.kernel_launches += 1;
     BQS_CK(cudaGetLastError());
     BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -259,7 +293,7 @@ int run_call(const Call& c, Stats& st) {
     if (host->status) return status_code(host->status);
     cur = host->lists[0];
   } else {
-    k_init_single<KT><<<1, 32, 0, s>>>(P, c.n);
+    k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
     st.kernel_launches += 1;
     if (c.n <= small_cutoff && c.n <= kWarpSortMax) cur.tiny = 1;
     else if (c.n <= small_cutoff) cur.small = 1;
@@ -267,12 +301,15 @@ int run_call(const Call& c, Stats& st) {
     else {
       cur.large = 1ull | ((unsigned long long)((c.n - 1) / tile + 1) << 32);
       cur.large_keys = (unsigned long long)c.n;
+      // mirrors inline_pivot(): which first segments leave their pivot to k_pivot
+      cur.todo = (P.depth_limit <= 0 || (P.pivot_rule == 1 && c.n >= 20000)) ? 1 : 0;
     }
   }
   BQS_CK(cudaGetLastError());
 
   const int sms = sm_count();
   const int part_grid_max = persistent_grid(var.fn, var.threads, var.smem);
+  const int local_grid = LocalCap<KT, PAIRS>::grid();
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
   size_t ev_used = 0;
 
@@ -287,8 +324,10 @@ int run_call(const Call& c, Stats& st) {
       st.levels += 1;
       st.partition_launches += 1;
       st.active_keys += (int64_t)cur.large_keys;
-      if (!c.partition_only) {
-        k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(nlarge, 8 * sms), 256, 0, s>>>(P);
+      // The counters of the lists this level produces start at zero.
+      BQS_CK(cudaMemsetAsync(&P.ctrl->lists[P.p ^ 1], 0, sizeof(ListCounts), s));
+      if (cur.todo) {
+        k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(cur.todo, 8 * sms), 256, 0, s>>>(P);
         st.kernel_launches += 1;
       }
       cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -308,6 +347,11 @@ int run_call(const Call& c, Stats& st) {
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 3;
+    }
+    if (cur.local) {
+      st.local_segments += cur.local;
+      LocalCap<KT, PAIRS>::launch(P, P.p, (int)std::min<uint32_t>(cur.local, (uint32_t)local_grid), s);
+      st.kernel_launches += 1;
     }
     if (cur.tiny) {
       st.small_segments += cur.tiny;

@@ -26,7 +26,7 @@ struct Options {
   int64_t depth_limit = -1;
   int64_t timing = 0;
   int64_t tile_variant = 0;
-  int64_t local_cutoff = 0;
+  int64_t local_cutoff = 0;    // -1: the largest segment one block holds; 0: off
 };
 
 struct Call {

@@ -1,11 +1,12 @@
 // sm_103a kernels of the level-synchronous BlockQuicksort.
 //
 //   k_init_*      first work lists from the caller's array / segments
-//   k_pivot       pivot of every large segment (Sec. 2 / Sec. 4 pivot rules)
+//   k_pivot       pivots that need a whole block (sqrt(n) sample, depth fallback)
 //   k_partition   Algorithm 3 per tile: compare, buffer outcomes, rearrange
+//                 (register-loading form; the TMA-fed form is in bqs_tma.cuh)
 //   k_bookkeep    children of every partitioned segment (Quicksort main loop)
-//   k_small_sort  sorting network for segments <= the small-segment cutoff
 //   k_fill        writes the class equal to a pivot into the final buffer
+// The small-segment sorting network is in bqs_small.cuh.
 #pragma once
 
 #include "bqs_common.cuh"
@@ -31,145 +32,6 @@ __device__ __forceinline__ int64_t isqrt64(int64_t n) {
   while (r * r > n) --r;
   while ((r + 1) * (r + 1) <= n) ++r;
   return r;
-}
-
-// Warp-cooperative append of one child segment per lane (`active` lanes with len > 0)
-// to the lists of level q: the sorting network (len <= small_cutoff), the single-block
-// sort (len <= local_cutoff) or another partition level.  Every lane of the warp must
-// call it.  Slots come from one atomic per warp and list; a large segment's slot and
-// first tile come from one packed 64-bit atomic, so tile0 grows with the slot index.
-template <class KT>
-__device__ void route_warp(const Params& P, int q, bool active, int64_t off, int64_t len,
-                           int parity, int depth) {
-  Ctrl* c = P.ctrl;
-  const int lane = threadIdx.x & 31;
-  const unsigned below = lanemask_lt();
-  const bool has = active && len > 0;
-  const bool sorted_now = has && len <= P.small_cutoff;
-  const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
-  const bool small = sorted_now && !tiny;                // one block per segment
-  const bool local = has && !sorted_now && len <= P.local_cutoff;
-  const bool large = has && !sorted_now && !local;
-
-#pragma unroll
-  for (int kind = 0; kind < 3; ++kind) {
-    const bool mine = kind == 0 ? tiny : kind == 1 ? small : local;
-    const unsigned m = __ballot_sync(~0u, mine);
-    if (!m) continue;
-    const int leader = __ffs(m) - 1;
-    unsigned int* counter = kind == 0 ? &c->lists[q].tiny : kind == 1 ? &c->lists[q].small : &c->lists[q].local;
-    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : P.l.local[q];
-    unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
-    base = __shfl_sync(~0u, base, leader);
-    if (mine) {
-      const unsigned int slot = base + __popc(m & below);
-      if (slot < P.l.cap_run) {
-        Run r;
-        r.off = off; r.len = len; r.parity = parity; r.pad = 0;
-        list[slot] = r;
-      } else {
-        atomicExch(&c->status, kStatusOverflow);
-      }
-    }
-  }
-
-  if (!__any_sync(~0u, large)) return;
-  const unsigned long long tiles = large ? (unsigned long long)((off + len - 1) / P.tile - off / P.tile + 1) : 0ull;
-  unsigned long long v = large ? (1ull | (tiles << 32)) : 0ull;
-  unsigned long long keys = large ? (unsigned long long)len : 0ull;
-  const unsigned long long own = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
-    const unsigned long long x = __shfl_up_sync(~0u, v, o);
-    if (lane >= o) v += x;
-    keys += __shfl_xor_sync(~0u, keys, o);
-  }
-  unsigned long long base = 0;
-  if (lane == 31) {
-    base = atomicAdd(&c->lists[q].large, v);
-    atomicAdd(&c->lists[q].large_keys, keys);
-  }
-  base = __shfl_sync(~0u, base, 31);
-  if (large) {
-    const unsigned long long old = base + v - own;   // exclusive prefix within the warp
-    const unsigned int slot = (unsigned int)old;
-    if (slot < P.l.cap_large) {
-      Seg s;
-      s.off = off; s.len = len; s.pkey = 0; s.pval = 0; s.depth = depth; s.parity = parity;
-      s.tile0 = (unsigned int)(old >> 32);
-      P.l.large[q][slot] = s;
-      P.l.cursor[q][slot] = 0ull;
-    } else {
-      atomicExch(&c->status, kStatusOverflow);
-    }
-  }
-}
-
-// ---- first work lists --------------------------------------------------------------------
-
-template <class KT>
-__global__ void k_init_single(Params P, int64_t n) {
-  if (blockIdx.x == 0 && threadIdx.x < 32) route_warp<KT>(P, 0, threadIdx.x == 0, 0, n, 0, 0);
-}
-
-// A single segment with a caller-given pivot (bqs_partition): always partitioned.
-template <class KT>
-__global__ void k_init_partition(Params P, int64_t n, uint64_t pkey) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    Seg s;
-    s.off = 0; s.len = n; s.pkey = pkey; s.pval = 0; s.depth = 0; s.parity = 0; s.tile0 = 0;
-    P.l.large[0][0] = s;
-    P.l.cursor[0][0] = 0ull;
-    P.ctrl->lists[0].large = 1ull | ((unsigned long long)((n - 1) / P.tile + 1) << 32);
-    P.ctrl->lists[0].large_keys = (unsigned long long)n;
-  }
-}
-
-// One thread per caller segment: check the offsets, then route the segment.
-template <class KT>
-__global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* __restrict__ offs,
-                                                       int64_t nseg) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    bool ok = false;
-    int64_t a = 0, b = 0;
-    if (i < nseg) {
-      a = offs[i];
-      b = offs[i + 1];
-      ok = a >= 0 && b >= a;
-      if (!ok) atomicExch(&P.ctrl->status, kStatusInvalid);
-    }
-    route_warp<KT>(P, 0, ok, a, b - a, 0, 0);
-  }
-}
-
-// ---- shared-memory sorting network --------------------------------------------------------
-
-// Bitonic sort (Batcher) of m = power-of-two (ord key, payload) entries in shared
-// memory, ascending, by all threads of the block.  Ends with a barrier.
-template <bool PAIRS, class U>
-__device__ void block_bitonic_sort(U* k, uint32_t* v, int m) {
-  for (int size = 2; size <= m; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < (m >> 1); i += blockDim.x) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        U a = k[lo], b = k[hi];
-        uint32_t va = 0, vb = 0;
-        if constexpr (PAIRS) { va = v[lo]; vb = v[hi]; }
-        const bool swap = up ? elem_less<PAIRS>(b, vb, a, va) : elem_less<PAIRS>(a, va, b, vb);
-        if (swap) {
-          k[lo] = b; k[hi] = a;
-          if constexpr (PAIRS) { v[lo] = vb; v[hi] = va; }
-        }
-      }
-    }
-  }
-  __syncthreads();
 }
 
 // ---- pivot selection ---------------------------------------------------------------------
@@ -215,15 +77,198 @@ __device__ Elem<KT, PAIRS> median5(Elem<KT, PAIRS>* e) {
   return e[2];
 }
 
-// One block per large segment: chooses the pivot and stores it in the descriptor.
-//  * median-of-3 of (first, middle, last) (Sec. 2);
-//  * sqrt rule (Sec. 4): below 64 keys median-of-3; below 20000 median-of-five-
-//    medians-of-five of 25 equally spaced keys; else the median of k = floor(sqrt(len))|1
+// Pivot rules one thread can evaluate (Sec. 2, Sec. 4): median-of-3 of (first, middle,
+// last); for the sqrt rule below 64 keys also median-of-3, below 20000 keys the
+// median-of-five-medians-of-five of 25 equally spaced keys.  Returns false when the
+// segment needs k_pivot instead (a sqrt(n) sample, or the depth-limit fallback).
+template <class KT, bool PAIRS>
+__device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity, int depth,
+                             uint64_t& pkey, uint32_t& pval) {
+  using E = Elem<KT, PAIRS>;
+  if (depth >= P.depth_limit) return false;
+  if (P.pivot_rule == 1 && len >= 20000) return false;
+  const typename KT::U* keys = (const typename KT::U*)P.b.key[parity];
+  const uint32_t* vals = P.b.val[parity];
+  E piv;
+  if (P.pivot_rule == 0 || len < 64) {
+    piv = median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, b),
+                             load_elem<KT, PAIRS>(keys, vals, b + len / 2),
+                             load_elem<KT, PAIRS>(keys, vals, b + len - 1));
+  } else {
+    E m[5];
+    for (int g = 0; g < 5; ++g) {
+      E e[5];
+      for (int j = 0; j < 5; ++j)
+        e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (5 * g + j) + 1) * len) / 50);
+      m[g] = median5<KT, PAIRS>(e);
+    }
+    piv = median5<KT, PAIRS>(m);
+  }
+  pkey = (uint64_t)KT::unord(piv.k);
+  pval = piv.v;
+  return true;
+}
+
+// Warp-cooperative append of one child segment per lane (`active` lanes with len > 0)
+// to the lists of level q: the sorting network (len <= small_cutoff), the single-block
+// sort (len <= local_cutoff) or another partition level.  Every lane of the warp must
+// call it.  Slots come from one atomic per warp and list; a large segment's slot and
+// first tile come from one packed 64-bit atomic, so tile0 grows with the slot index.
+// A large segment's pivot is chosen here when one thread can do it; otherwise the
+// segment is queued on `todo` for k_pivot.
+template <class KT, bool PAIRS>
+__device__ void route_warp(const Params& P, int q, bool active, int64_t off, int64_t len,
+                           int parity, int depth) {
+  Ctrl* c = P.ctrl;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = lanemask_lt();
+  const bool has = active && len > 0;
+  const bool sorted_now = has && len <= P.small_cutoff;
+  const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
+  const bool small = sorted_now && !tiny;                // one block per segment
+  const bool local = has && !sorted_now && len <= P.local_cutoff;
+  const bool large = has && !sorted_now && !local;
+
+#pragma unroll
+  for (int kind = 0; kind < 3; ++kind) {
+    const bool mine = kind == 0 ? tiny : kind == 1 ? small : local;
+    const unsigned m = __ballot_sync(~0u, mine);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    unsigned int* counter = kind == 0 ? &c->lists[q].tiny : kind == 1 ? &c->lists[q].small : &c->lists[q].local;
+    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : P.l.local[q];
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    base = __shfl_sync(~0u, base, leader);
+    if (mine) {
+      const unsigned int slot = base + __popc(m & below);
+      if (slot < P.l.cap_run) {
+        Run r;
+        r.off = off; r.len = len; r.parity = parity; r.pad = 0;
+        list[slot] = r;
+      } else {
+        atomicExch(&c->status, kStatusOverflow);
+      }
+    }
+  }
+
+  if (!__any_sync(~0u, large)) return;
+  const unsigned long long tiles = large ? (unsigned long long)tile_count(off, len, P.tile) : 0ull;
+  unsigned long long v = large ? (1ull | (tiles << 32)) : 0ull;
+  unsigned long long keys = large ? (unsigned long long)len : 0ull;
+  const unsigned long long own = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
+    const unsigned long long x = __shfl_up_sync(~0u, v, o);
+    if (lane >= o) v += x;
+    keys += __shfl_xor_sync(~0u, keys, o);
+  }
+  unsigned long long base = 0;
+  if (lane == 31) {
+    base = atomicAdd(&c->lists[q].large, v);
+    atomicAdd(&c->lists[q].large_keys, keys);
+  }
+  base = __shfl_sync(~0u, base, 31);
+  const unsigned long long old = base + v - own;   // exclusive prefix within the warp
+  const unsigned int slot = (unsigned int)old;
+  bool needs_kernel = false;
+  if (large) {
+    if (slot < P.l.cap_large) {
+      Seg s;
+      s.off = off; s.len = len; s.pkey = 0; s.pval = 0; s.depth = depth; s.parity = parity;
+      s.tile0 = (unsigned int)(old >> 32);
+      needs_kernel = !inline_pivot<KT, PAIRS>(P, off, len, parity, depth, s.pkey, s.pval);
+      P.l.large[q][slot] = s;
+      P.l.cursor[q][slot] = 0ull;
+    } else {
+      atomicExch(&c->status, kStatusOverflow);
+    }
+  }
+  const unsigned m = __ballot_sync(~0u, needs_kernel);
+  if (m) {
+    const int leader = __ffs(m) - 1;
+    unsigned int tb = 0;
+    if (lane == leader) tb = atomicAdd(&c->lists[q].todo, (unsigned)__popc(m));
+    tb = __shfl_sync(~0u, tb, leader);
+    if (needs_kernel) P.l.todo[q][tb + __popc(m & below)] = slot;
+  }
+}
+
+// ---- first work lists --------------------------------------------------------------------
+
+template <class KT, bool PAIRS>
+__global__ void k_init_single(Params P, int64_t n) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) route_warp<KT, PAIRS>(P, 0, threadIdx.x == 0, 0, n, 0, 0);
+}
+
+// A single segment with a caller-given pivot (bqs_partition): always partitioned.
+template <class KT>
+__global__ void k_init_partition(Params P, int64_t n, uint64_t pkey) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Seg s;
+    s.off = 0; s.len = n; s.pkey = pkey; s.pval = 0; s.depth = 0; s.parity = 0; s.tile0 = 0;
+    P.l.large[0][0] = s;
+    P.l.cursor[0][0] = 0ull;
+    P.ctrl->lists[0].large = 1ull | ((unsigned long long)((n - 1) / P.tile + 1) << 32);
+    P.ctrl->lists[0].large_keys = (unsigned long long)n;
+  }
+}
+
+// One thread per caller segment: check the offsets, then route the segment.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* __restrict__ offs,
+                                                       int64_t nseg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool ok = false;
+    int64_t a = 0, b = 0;
+    if (i < nseg) {
+      a = offs[i];
+      b = offs[i + 1];
+      ok = a >= 0 && b >= a;
+      if (!ok) atomicExch(&P.ctrl->status, kStatusInvalid);
+    }
+    route_warp<KT, PAIRS>(P, 0, ok, a, b - a, 0, 0);
+  }
+}
+
+// ---- shared-memory sorting network --------------------------------------------------------
+
+// Bitonic sort (Batcher) of m = power-of-two (ord key, payload) entries in shared
+// memory, ascending, by all threads of the block.  Ends with a barrier.
+template <bool PAIRS, class U>
+__device__ void block_bitonic_sort(U* k, uint32_t* v, int m) {
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < (m >> 1); i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        U a = k[lo], b = k[hi];
+        uint32_t va = 0, vb = 0;
+        if constexpr (PAIRS) { va = v[lo]; vb = v[hi]; }
+        const bool swap = up ? elem_less<PAIRS>(b, vb, a, va) : elem_less<PAIRS>(a, va, b, vb);
+        if (swap) {
+          k[lo] = b; k[hi] = a;
+          if constexpr (PAIRS) { v[lo] = vb; v[hi] = va; }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- pivot selection kernel ---------------------------------------------------------------
+
+// One block per large segment whose pivot needs the whole block (the list `todo`):
+//  * sqrt rule (Sec. 4) at 20000 keys and more: the median of k = floor(sqrt(len))|1
 //    equally spaced keys (k capped at kMaxSample), sorted in shared memory;
 //  * a segment at the depth limit gets the midpoint of its ord-key range (payload
 //    range when all its keys are equal): each such level halves the range, so the
 //    recursion depth stays bounded by the key width (the role Heapsort plays in Sec. 2).
-// Block 0 also clears the counters of the lists this level is about to produce.
+// All other pivots are chosen by route_warp when the segment is created.
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_pivot(Params P) {
   using U = typename KT::U;
@@ -233,14 +278,10 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   __shared__ U s_red[2][8];
   __shared__ uint32_t s_redv[2][8];
 
-  const int q = P.p ^ 1;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    P.ctrl->lists[q].large = 0; P.ctrl->lists[q].fill = 0; P.ctrl->lists[q].large_keys = 0;
-    P.ctrl->lists[q].small = 0; P.ctrl->lists[q].local = 0; P.ctrl->lists[q].tiny = 0;
-  }
-  const unsigned int count = min((unsigned int)P.ctrl->lists[P.p].large, P.l.cap_large);
+  const unsigned int count = min(P.ctrl->lists[P.p].todo, P.l.cap_large);
   Seg* segs = P.l.large[P.p];
-  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
+  for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
+    const unsigned int s = P.l.todo[P.p][i];
     const Seg sg = segs[s];
     const U* keys = (const U*)P.b.key[sg.parity];
     const uint32_t* vals = P.b.val[sg.parity];
@@ -290,22 +331,6 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
         piv.v = vmin + (vmax - vmin) / 2;
       }
       if (threadIdx.x == 0) atomicAdd(&P.ctrl->fallbacks, 1ull);
-    } else if (P.pivot_rule == 0 || len < 64) {
-      if (threadIdx.x == 0)
-        piv = median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, b),
-                                 load_elem<KT, PAIRS>(keys, vals, b + len / 2),
-                                 load_elem<KT, PAIRS>(keys, vals, b + len - 1));
-    } else if (len < 20000) {
-      if (threadIdx.x == 0) {
-        E m[5];
-        for (int g = 0; g < 5; ++g) {
-          E e[5];
-          for (int j = 0; j < 5; ++j)
-            e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (5 * g + j) + 1) * len) / 50);
-          m[g] = median5<KT, PAIRS>(e);
-        }
-        piv = median5<KT, PAIRS>(m);
-      }
     } else {
       int64_t k = isqrt64(len) | 1;
       if (k > kMaxSample) k = kMaxSample;
@@ -395,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition(Params P) {
       U* __restrict__ dst = (U*)P.b.key[sg.parity ^ 1];
       const uint32_t* __restrict__ vsrc = P.b.val[sg.parity];
       uint32_t* __restrict__ vdst = P.b.val[sg.parity ^ 1];
-      const int64_t abase = (sg.off / TILE) * TILE + (int64_t)(t - sg.tile0) * TILE;
+      const int64_t abase = tile_origin(sg.off) + (int64_t)(t - sg.tile0) * TILE;
       const int64_t lo = max(abase, sg.off), hi = min(abase + TILE, sg.off + sg.len);
       const U pk = KT::ord((U)sg.pkey);
       const uint32_t pv = sg.pval;
@@ -567,40 +592,9 @@ __global__ void __launch_bounds__(256) k_bookkeep(Params P) {
       }
     }
     if (P.route_children) {   // both sides exclude the pivot class (Sec. 2)
-      route_warp<KT>(P, q, active, sg.off, nlt, sg.parity ^ 1, sg.depth + 1);
-      route_warp<KT>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
+      route_warp<KT, PAIRS>(P, q, active, sg.off, nlt, sg.parity ^ 1, sg.depth + 1);
+      route_warp<KT, PAIRS>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
     }
-  }
-}
-
-// ---- small-segment sort ----------------------------------------------------------------
-
-// One block per segment of at most kMaxSmall keys: load into shared memory (padded
-// with the largest order key), bitonic sort, write into the final buffer.
-template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(256) k_small_sort(Params P, int p) {
-  using U = typename KT::U;
-  __shared__ __align__(16) U s_k[kMaxSmall];
-  __shared__ __align__(16) uint32_t s_v[PAIRS ? kMaxSmall : 1];
-  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
-  const Run* runs = P.l.small[p];
-  U* fk = (U*)P.b.final_key;
-  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
-    const Run r = runs[s];
-    const U* src = (const U*)P.b.key[r.parity];
-    const uint32_t* vsrc = P.b.val[r.parity];
-    const int len = (int)r.len;
-    const int m = next_pow2(len < 2 ? 2 : len);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      s_k[i] = i < len ? KT::ord(src[r.off + i]) : ~U(0);
-      if constexpr (PAIRS) s_v[i] = i < len ? vsrc[r.off + i] : 0xFFFFFFFFu;
-    }
-    block_bitonic_sort<PAIRS>(s_k, s_v, m);
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-      fk[r.off + i] = KT::unord(s_k[i]);
-      if constexpr (PAIRS) P.b.final_val[r.off + i] = s_v[i];
-    }
-    __syncthreads();
   }
 }
 

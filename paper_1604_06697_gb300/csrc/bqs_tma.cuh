@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
   auto issue = [&](uint32_t i) {
     const int st = i % STAGES;
     const TileInfo& ti = s_info[((i / CHUNK) & 1) * CHUNK + (i % CHUNK)];
-    const int64_t abase = (ti.off / TILE) * TILE + (int64_t)(ti.parity >> 1) * TILE;
+    const int64_t abase = tile_origin(ti.off) + (int64_t)(ti.parity >> 1) * TILE;
     const int64_t lo = max(abase, ti.off), hi = min(abase + TILE, ti.off + ti.len);
     const int64_t n4 = n_total & ~(int64_t)3;
     const int64_t b0 = lo & ~(int64_t)3;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
     if (s_abort) break;
 
     const TileInfo ti = s_info[((i / CHUNK) & 1) * CHUNK + (i % CHUNK)];
-    const int64_t abase = (ti.off / TILE) * TILE + (int64_t)(ti.parity >> 1) * TILE;
+    const int64_t abase = tile_origin(ti.off) + (int64_t)(ti.parity >> 1) * TILE;
     const int lo = (int)(max(abase, ti.off) - abase);
     const int hi = (int)(min(abase + TILE, ti.off + ti.len) - abase);
     const bool full = lo == 0 && hi == TILE;

@@ -83,6 +83,23 @@ def test_small_cutoffs(bqs, cutoff):
             assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
 
 
+@pytest.mark.parametrize("local", [-1, 0, 3000, 16384])
+@pytest.mark.parametrize("cutoff", [16, 256, 2048])
+def test_local_sort_cutoffs(bqs, cutoff, local):
+    # Segments above the small cutoff and up to the local cutoff are finished by one
+    # block in shared memory; 0 turns that off (every such segment is partitioned).
+    bqs.set_option("small_cutoff", cutoff)
+    bqs.set_option("local_cutoff", local)
+    for dtype in DTYPES:
+        for n, dist in [(257, "uniform"), (2049, "reversed"), (16384, "uniform"),
+                        (16385, "mod_sqrt"), (300_001, "uniform"), (100_000, "all_equal"),
+                        (200_000, "swapped_1pct")]:
+            a = inputs.make_keys(n, dtype, dist, seed=n + cutoff)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+    if local != 0:
+        assert bqs.stats()["local_segments"] > 0
+
+
 def test_float64_special_values(bqs):
     vals = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, 5e-324, -5e-324, 2.5, -2.5,
                      np.finfo(np.float64).max, -np.finfo(np.float64).max] * 500)
