@@ -51,7 +51,8 @@ typedef enum {
   BQS_ERR_NOMEM = -2,       /* scratch memory could not be obtained */
   BQS_ERR_CUDA = -3,        /* a CUDA call or kernel launch failed */
   BQS_ERR_TIMEOUT = -4,     /* a device-side bounded wait ran out */
-  BQS_ERR_UNSUPPORTED = -5  /* option or combination not provided */
+  BQS_ERR_UNSUPPORTED = -5, /* option or combination not provided */
+  BQS_ERR_TOO_LARGE = -7    /* bqs_sort_noalloc: n above its fixed scratch */
 } bqs_status;
 
 /* A pivot value for bqs_partition.  dtype selects the member of v that is read. */
@@ -113,6 +114,30 @@ int bqs_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int
  *   vals  device, n uint32 payloads, moved with their keys.
  */
 int bqs_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, bqs_stream_t stream);
+
+/*
+ * bqs_sort_noalloc -- bqs_sort for callers that cannot allocate device memory when
+ * they sort (for example a service that reserves all of its GPU memory at start-up
+ * and must not grow it or fail with out-of-memory mid-request, or code running
+ * inside a framework whose allocator owns the device memory).  The paper has no
+ * counterpart; this is a deployment variant of bqs_sort with the same result.
+ *
+ *   keys, n, dtype, stream  as for bqs_sort; keys is the caller's device array.
+ *   Limit: n <= 2^20 keys (any dtype).  Larger n returns BQS_ERR_TOO_LARGE without
+ *          touching the GPU; so do option settings whose work lists would not fit.
+ * Scratch: a fixed 16 MiB array in the library's device data (allocated when the
+ * library is loaded, held by every GPU that loads it until the process exits).  No
+ * device or pinned host memory is allocated or freed: no cudaMalloc, cudaMallocAsync,
+ * cudaMallocHost or cudaFree call.  The first call on a device looks up that array's
+ * device address for
+ * the device (cudaGetSymbolAddress) and sets up the kernels; make that first call
+ * before any stream capture.  All calls share the one array and every call starts
+ * by clearing the parts it relies on, so earlier contents do not matter, but calls
+ * whose work overlaps on the GPU (different streams or threads at the same time)
+ * race on it: serialise them.  Synchronous with respect to `stream` between
+ * partition levels, like bqs_sort.
+ */
+int bqs_sort_noalloc(void* keys, int64_t n, int32_t dtype, bqs_stream_t stream);
 
 /* Process-wide options, read at the start of each call. */
 typedef enum {

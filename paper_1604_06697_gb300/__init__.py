@@ -57,6 +57,23 @@ def sort(keys, stream=None):
     return keys
 
 
+NOALLOC_MAX_KEYS = 1 << 20
+
+
+def sort_noalloc(keys, stream=None):
+    """Sorts like sort() without allocating any memory during the call.
+
+    For callers that cannot allocate device memory while they sort (memory
+    reserved up front, or owned by another framework's allocator).  Uses a fixed
+    scratch array held by the library; n is limited to NOALLOC_MAX_KEYS.  Calls
+    that run on the GPU at the same time share that array and must be serialised.
+    """
+    _require_cuda(keys)
+    _check(_native.lib().bqs_sort_noalloc(keys.data_ptr(), keys.numel(), _dtype_code(keys),
+                                          _stream_ptr(keys, stream)), "bqs_sort_noalloc")
+    return keys
+
+
 def sort_pairs(keys, vals, stream=None):
     """Sorts (key, uint32 payload) pairs in place by (key, payload).
 

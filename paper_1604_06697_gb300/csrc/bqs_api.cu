@@ -45,6 +45,16 @@ int dispatch(int32_t dtype, const Call& c) {
 }
 }  // namespace
 
+Options current_options() { return snapshot_options(); }
+
+void clear_stats() { t_stats = Stats{}; }
+
+int dispatch_call(int32_t dtype, const Call& c) { return dispatch(dtype, c); }
+
+int64_t layout_bytes(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff) {
+  return (int64_t)plan_layout(n, key_size, pairs, nseg, small_cutoff, true).total;
+}
+
 int fail_cuda(cudaError_t e, const char* what) {
   std::snprintf(t_err, sizeof t_err, "CUDA error in %s: %s", what, cudaGetErrorString(e));
   cudaGetLastError();
@@ -266,6 +276,8 @@ const char* bqs_status_string(int status) {
     case BQS_ERR_TIMEOUT: return "device-side wait timed out";
     case BQS_ERR_UNSUPPORTED: return "unsupported option or combination";
     case kErrInternal: return "internal work list overflow";
+    case BQS_ERR_TOO_LARGE:
+      return "n exceeds the fixed scratch of bqs_sort_noalloc (at most 2^20 keys)";
     default: return "unknown status";
   }
 }

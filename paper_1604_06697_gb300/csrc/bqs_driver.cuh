@@ -237,7 +237,13 @@ int run_call(const Call& c, Stats& st) {
 
   const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only);
   Scratch scratch;
-  int rc = acquire_scratch(scratch, L.total, s);
+  int rc = kOk;
+  if (c.fixed_ws) {   // allocation-free call: the caller's fixed scratch must be enough
+    if ((size_t)c.fixed_ws_bytes < L.total) return kErrInvalid;
+    scratch.base = (char*)c.fixed_ws;
+  } else {
+    rc = acquire_scratch(scratch, L.total, s);
+  }
   if (rc) return rc;
   char* w = scratch.base;
 
@@ -274,7 +280,9 @@ int run_call(const Call& c, Stats& st) {
     P.depth_limit = c.opt.depth_limit >= 0 ? (int)c.opt.depth_limit : 2 * lg + 3;
   }
 
-  Ctrl* host = pinned_ctrl();
+  static thread_local Ctrl pageable_ctrl;
+  Ctrl* host = c.fixed_ws ? &pageable_ctrl : pinned_ctrl();
+  const bool timing = c.opt.timing && !c.fixed_ws;
   BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
 
   ListCounts cur{};
@@ -331,7 +339,7 @@ int run_call(const Call& c, Stats& st) {
         st.kernel_launches += 1;
       }
       cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (c.opt.timing) {
+      if (timing) {
         if (ev_used == evs.size()) {
           cudaEvent_t a, b;
           BQS_CK(cudaEventCreate(&a));
@@ -343,7 +351,7 @@ int run_call(const Call& c, Stats& st) {
         BQS_CK(cudaEventRecord(e0, s));
       }
       var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s);
-      if (c.opt.timing) BQS_CK(cudaEventRecord(e1, s));
+      if (timing) BQS_CK(cudaEventRecord(e1, s));
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 3;
@@ -382,7 +390,7 @@ int run_call(const Call& c, Stats& st) {
   st.equal_keys = (int64_t)host->equal_keys;
   st.fallback_pivots = (int64_t)host->fallbacks;
   st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
-  if (c.opt.timing && ev_used) {
+  if (timing && ev_used) {
     BQS_CK(cudaStreamSynchronize(s));
     double ms = 0;
     for (size_t i = 0; i < ev_used; ++i) {

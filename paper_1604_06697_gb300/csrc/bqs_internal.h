@@ -41,6 +41,10 @@ struct Call {
   int64_t* split = nullptr;
   void* stream = nullptr;
   Options opt;
+  // Allocation-free calls only (bqs_sort_noalloc): a fixed device scratch area to use
+  // instead of any allocation, and no pinned host buffer or timing events either.
+  void* fixed_ws = nullptr;
+  int64_t fixed_ws_bytes = 0;
 };
 
 struct Stats {
@@ -52,6 +56,10 @@ struct Stats {
 
 // Implemented in bqs_api.cu.
 int fail_cuda(cudaError_t e, const char* what);
+Options current_options();
+void clear_stats();
+int dispatch_call(int32_t dtype, const Call& c);   // runs c, keeps its statistics
+int64_t layout_bytes(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff);
 void user_workspace(void** ptr, int64_t* bytes);
 void prepare_mempool();
 Ctrl* pinned_ctrl();
