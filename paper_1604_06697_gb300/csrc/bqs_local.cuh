@@ -72,6 +72,11 @@ __device__ __forceinline__ void warp_sort_leaf(const typename KT::U* src, const 
   else warp_sort_smem<KT, PAIRS, 8>(src, vsrc, dst, vdst, len, lane);
 }
 
+// Leaves are recorded as begin | (len - 1) << 15 | buffer << 24 (begin < 2^15, len <= 256).
+__device__ __forceinline__ uint32_t pack_leaf(int begin, int len, int buf) {
+  return (uint32_t)begin | ((uint32_t)(len - 1) << 15) | ((uint32_t)buf << 24);
+}
+
 template <class KT, bool PAIRS, int L, int T>
 __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
   using U = typename KT::U;
@@ -79,24 +84,35 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
   using E = Elem<KT, PAIRS>;
   constexpr int WARPS = T / 32;
   constexpr int KPL = kLocalChunk / 32;
+  constexpr int MAXLEAF = 2048;
   static_assert(L / (kLocalLeaf + 1) + 1 <= kLocalMaxAct, "active list capacity");
+  static_assert(L <= 32768 && kLocalLeaf <= 256, "leaf record packing");
 
   extern __shared__ __align__(16) unsigned char smem[];
-  U* kbuf[2] = {reinterpret_cast<U*>(smem), reinterpret_cast<U*>(smem + S::kbuf)};
-  uint32_t* vbuf[2] = {reinterpret_cast<uint32_t*>(smem + 2 * S::kbuf),
-                       reinterpret_cast<uint32_t*>(smem + 2 * S::kbuf + S::vbuf)};
+  // buffer b: keys at smem + b*kbuf, payloads at smem + 2*kbuf + b*vbuf
+  auto kb = [&](int b) { return reinterpret_cast<U*>(smem + (size_t)b * S::kbuf); };
+  auto vb = [&](int b) { return reinterpret_cast<uint32_t*>(smem + 2 * S::kbuf + (size_t)b * S::vbuf); };
   __shared__ SubSeg s_act[2][kLocalMaxAct];
   __shared__ U s_pk[kLocalMaxAct];            // pivot of each active sub-segment (raw bits)
   __shared__ uint32_t s_pv[kLocalMaxAct];
   __shared__ uint32_t s_vstart[kLocalMaxAct + 1];  // work-item starts, padded to kLocalChunk
   __shared__ uint32_t s_cnt[kLocalMaxAct];    // (#<) | (#>) << 16 claimed so far
-  __shared__ SubSeg s_leaf[2 * kLocalMaxAct];
-  __shared__ int3 s_eq[kLocalMaxAct];         // (begin, len, parent) of pivot-class runs
-  __shared__ int s_nact[2], s_nleaf, s_neq;
+  __shared__ uint32_t s_leaf[MAXLEAF];
+  __shared__ int s_nact[2], s_nleaf;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned int count = min(P.ctrl->lists[p].local, P.l.cap_run);
   const int depth_cap = 2 * (31 - __clz(L)) + 8;   // local Introsort-style limit
+
+  // Sorts every recorded leaf into buffer 0, warps taking leaves round-robin.
+  auto flush_leaves = [&]() {
+    const int nl = s_nleaf;
+    for (int f = warp; f < nl; f += WARPS) {
+      const uint32_t q = s_leaf[f];
+      const int b = (int)(q & 0x7FFF), ln = (int)((q >> 15) & 0x1FF) + 1, bf = (int)(q >> 24);
+      warp_sort_leaf<KT, PAIRS>(kb(bf) + b, vb(bf) + b, kb(0) + b, vb(0) + b, ln, lane);
+    }
+  };
 
   for (unsigned int r = blockIdx.x; r < count; r += gridDim.x) {
     const Run run = P.l.local[p][r];
@@ -104,17 +120,19 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
     {
       const U* g = (const U*)P.b.key[run.parity] + run.off;
       const uint32_t* gv = PAIRS ? P.b.val[run.parity] + run.off : nullptr;
+      U* k0 = kb(0);
+      uint32_t* v0 = vb(0);
       for (int i = tid; i < len; i += T) {
-        kbuf[0][i] = g[i];
-        if constexpr (PAIRS) vbuf[0][i] = gv[i];
+        k0[i] = g[i];
+        if constexpr (PAIRS) v0[i] = gv[i];
       }
     }
     if (tid == 0) {
       s_nleaf = 0;
-      s_neq = 0;
+      s_nact[1] = 0;
       if (len <= kLocalLeaf) {
         s_nact[0] = 0;
-        s_leaf[0] = SubSeg{0, len, 0, 0};
+        s_leaf[0] = pack_leaf(0, len, 0);
         s_nleaf = 1;
       } else {
         s_nact[0] = 1;
@@ -125,41 +143,33 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
 
     for (int cur = 0;; cur ^= 1) {
       const int nact = s_nact[cur];
-      // Leaves from the previous level (or the segment itself) and pivot-class runs.
-      for (int e = warp; e < s_neq; e += WARPS) {
-        const int3 q = s_eq[e];
-        for (int i = lane; i < q.y; i += 32) {
-          kbuf[0][q.x + i] = s_pk[q.z];
-          if constexpr (PAIRS) vbuf[0][q.x + i] = s_pv[q.z];
-        }
-      }
-      for (int f = warp; f < s_nleaf; f += WARPS) {
-        const SubSeg a = s_leaf[f];
-        warp_sort_leaf<KT, PAIRS>(kbuf[a.buf] + a.begin, vbuf[a.buf] + a.begin,
-                                  kbuf[0] + a.begin, vbuf[0] + a.begin, a.len, lane);
-      }
       if (nact == 0) break;
-      __syncthreads();
+      // Keep room for this level's leaves (at most two per active sub-segment).
+      if (s_nleaf + 2 * nact > MAXLEAF) {
+        flush_leaves();
+        __syncthreads();
+        if (tid == 0) s_nleaf = 0;
+      }
 
       // Pivots (median of three medians of three of nine spaced keys; the midpoint of
       // the ord-key range past the local depth cap) and work-item starts.
       if (tid < nact) {
         const SubSeg a = s_act[cur][tid];
-        const U* kb = kbuf[a.buf] + a.begin;
-        const uint32_t* vb = vbuf[a.buf] + a.begin;
+        const U* kk = kb(a.buf) + a.begin;
+        const uint32_t* vv = vb(a.buf) + a.begin;
         E piv;
         if (a.depth < depth_cap) {
           E m[3];
           for (int g = 0; g < 3; ++g)
             m[g] = median3<KT, PAIRS>(
-                load_elem<KT, PAIRS>(kb, vb, ((2 * (3 * g + 0) + 1) * a.len) / 18),
-                load_elem<KT, PAIRS>(kb, vb, ((2 * (3 * g + 1) + 1) * a.len) / 18),
-                load_elem<KT, PAIRS>(kb, vb, ((2 * (3 * g + 2) + 1) * a.len) / 18));
+                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 0) + 1) * a.len) / 18),
+                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 1) + 1) * a.len) / 18),
+                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 2) + 1) * a.len) / 18));
           piv = median3<KT, PAIRS>(m[0], m[1], m[2]);
         } else {
           U kmin = ~U(0), kmax = 0;
           for (int i = 0; i < a.len; ++i) {
-            const U k = KT::ord(kb[i]);
+            const U k = KT::ord(kk[i]);
             kmin = k < kmin ? k : kmin;
             kmax = k > kmax ? k : kmax;
           }
@@ -168,8 +178,8 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
           if (PAIRS && kmin == kmax) {
             uint32_t vmin = 0xFFFFFFFFu, vmax = 0;
             for (int i = 0; i < a.len; ++i) {
-              vmin = min(vmin, vb[i]);
-              vmax = max(vmax, vb[i]);
+              vmin = min(vmin, vv[i]);
+              vmax = max(vmax, vv[i]);
             }
             piv.v = vmin + (vmax - vmin) / 2;
           }
@@ -198,11 +208,7 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
           if (j <= nact) s_vstart[j] = run_;
           run_ += v[i];
         }
-        if (lane == 0) {
-          s_nact[cur ^ 1] = 0;
-          s_nleaf = 0;
-          s_neq = 0;
-        }
+        if (lane == 0) s_nact[cur ^ 1] = 0;
       }
       __syncthreads();
 
@@ -218,10 +224,10 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
         const int j = lo;
         const SubSeg a = s_act[cur][j];
         const int base = (int)(v0 - s_vstart[j]);
-        const U* src = kbuf[a.buf] + a.begin;
-        const uint32_t* vsrc = vbuf[a.buf] + a.begin;
-        U* dst = kbuf[a.buf ^ 1] + a.begin;
-        uint32_t* vdst = vbuf[a.buf ^ 1] + a.begin;
+        const U* src = kb(a.buf) + a.begin;
+        const uint32_t* vsrc = vb(a.buf) + a.begin;
+        U* dst = kb(a.buf ^ 1) + a.begin;
+        uint32_t* vdst = vb(a.buf ^ 1) + a.begin;
         const U pk = s_pk[j];
         const U pko = KT::ord(pk);
         const uint32_t pv = s_pv[j];
@@ -272,31 +278,42 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
       }
       __syncthreads();
 
-      // Children of every active sub-segment.
+      // Children of every active sub-segment; the pivot class is final: it is written
+      // to buffer 0 right away (usually a single key).
       if (tid < nact) {
         const SubSeg a = s_act[cur][tid];
         const int nlt = (int)(s_cnt[tid] & 0xFFFF), ngt = (int)(s_cnt[tid] >> 16);
         const int neq = a.len - nlt - ngt;
-        if (neq > 0) s_eq[atomicAdd(&s_neq, 1)] = make_int3(a.begin + nlt, neq, tid);
+        U* k0 = kb(0) + a.begin + nlt;
+        uint32_t* v0 = vb(0) + a.begin + nlt;
+        for (int i = 0; i < neq; ++i) {
+          k0[i] = s_pk[tid];
+          if constexpr (PAIRS) v0[i] = s_pv[tid];
+        }
         const SubSeg kids[2] = {SubSeg{a.begin, nlt, a.buf ^ 1, a.depth + 1},
                                 SubSeg{a.begin + a.len - ngt, ngt, a.buf ^ 1, a.depth + 1}};
         for (int c = 0; c < 2; ++c) {
           if (kids[c].len == 0) continue;
-          if (kids[c].len <= kLocalLeaf) s_leaf[atomicAdd(&s_nleaf, 1)] = kids[c];
-          else s_act[cur ^ 1][atomicAdd(&s_nact[cur ^ 1], 1)] = kids[c];
+          if (kids[c].len <= kLocalLeaf)
+            s_leaf[atomicAdd(&s_nleaf, 1)] = pack_leaf(kids[c].begin, kids[c].len, kids[c].buf);
+          else
+            s_act[cur ^ 1][atomicAdd(&s_nact[cur ^ 1], 1)] = kids[c];
         }
       }
       __syncthreads();
     }
+    flush_leaves();
     __syncthreads();
 
     // The assembled segment goes to the final buffer once.
     {
       U* g = (U*)P.b.final_key + run.off;
       uint32_t* gv = PAIRS ? P.b.final_val + run.off : nullptr;
+      const U* k0 = kb(0);
+      const uint32_t* v0 = vb(0);
       for (int i = tid; i < len; i += T) {
-        g[i] = kbuf[0][i];
-        if constexpr (PAIRS) gv[i] = vbuf[0][i];
+        g[i] = k0[i];
+        if constexpr (PAIRS) gv[i] = v0[i];
       }
     }
     __syncthreads();

@@ -26,70 +26,138 @@ __device__ __forceinline__ U shfl_xor_any(U x, int d) {
   }
 }
 
-// Compare-exchange of two register entries: afterwards (a, b) is ordered ascending
-// when `up`, descending otherwise.
-template <bool PAIRS, class U>
-__device__ __forceinline__ void cx(U& a, uint32_t& va, U& b, uint32_t& vb, bool up) {
-  const bool sw = up ? elem_less<PAIRS>(b, vb, a, va) : elem_less<PAIRS>(a, va, b, vb);
-  const U ta = sw ? b : a, tb = sw ? a : b;
-  a = ta;
-  b = tb;
-  if constexpr (PAIRS) {
-    const uint32_t tva = sw ? vb : va, tvb = sw ? va : vb;
-    va = tva;
-    vb = tvb;
+// A thread's row of R consecutive entries in shared memory, moved with 16-byte (or
+// 8-byte) accesses: a warp then touches consecutive 16-byte words and no bank twice
+// beyond the minimum number of wavefronts.
+template <int R, class U>
+__device__ __forceinline__ void store_row(U* dst, const U (&x)[R]) {
+  constexpr int BYTES = R * (int)sizeof(U);
+  if constexpr (BYTES % 16 == 0) {
+    constexpr int PER = 16 / (int)sizeof(U);
+#pragma unroll
+    for (int c = 0; c < BYTES / 16; ++c) {
+      union { uint4 v; U e[PER]; } u;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) u.e[e] = x[c * PER + e];
+      reinterpret_cast<uint4*>(dst)[c] = u.v;
+    }
+  } else if constexpr (BYTES == 8) {
+    union { uint2 v; U e[8 / sizeof(U)]; } u;
+#pragma unroll
+    for (int e = 0; e < R; ++e) u.e[e] = x[e];
+    *reinterpret_cast<uint2*>(dst) = u.v;
+  } else {
+#pragma unroll
+    for (int e = 0; e < R; ++e) dst[e] = x[e];
   }
 }
 
-// Sorts the m = R*T entries held as x[R], y[R] by the T = blockDim-participating threads
-// (t = thread index within the group).  s_x / s_y: shared scratch of m entries, used
-// only for exchanges between warps (T > 32).  Entries are ord images (+ payloads).
+template <int R, class U>
+__device__ __forceinline__ void load_row(const U* src, U (&x)[R]) {
+  constexpr int BYTES = R * (int)sizeof(U);
+  if constexpr (BYTES % 16 == 0) {
+    constexpr int PER = 16 / (int)sizeof(U);
+#pragma unroll
+    for (int c = 0; c < BYTES / 16; ++c) {
+      union { uint4 v; U e[PER]; } u;
+      u.v = reinterpret_cast<const uint4*>(src)[c];
+#pragma unroll
+      for (int e = 0; e < PER; ++e) x[c * PER + e] = u.e[e];
+    }
+  } else if constexpr (BYTES == 8) {
+    union { uint2 v; U e[8 / sizeof(U)]; } u;
+    u.v = *reinterpret_cast<const uint2*>(src);
+#pragma unroll
+    for (int e = 0; e < R; ++e) x[e] = u.e[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < R; ++e) x[e] = src[e];
+  }
+}
+
+template <class U>
+__device__ __forceinline__ U umin_(U a, U b) { return a < b ? a : b; }
+template <class U>
+__device__ __forceinline__ U umax_(U a, U b) { return a < b ? b : a; }
+
+// Ascending compare-exchange of two register entries: afterwards a <= b.
+template <bool PAIRS, class U>
+__device__ __forceinline__ void cx_up(U& a, uint32_t& va, U& b, uint32_t& vb) {
+  if constexpr (PAIRS) {
+    const bool sw = elem_less<PAIRS>(b, vb, a, va);
+    const U ta = sw ? b : a, tb = sw ? a : b;
+    const uint32_t tva = sw ? vb : va, tvb = sw ? va : vb;
+    a = ta; b = tb; va = tva; vb = tvb;
+  } else {
+    const U lo = umin_(a, b), hi = umax_(a, b);
+    a = lo;
+    b = hi;
+  }
+}
+
+// Keeps the smaller (keep_min) or larger of an entry and its partner's.
+template <bool PAIRS, class U>
+__device__ __forceinline__ void keep_one(U& x, uint32_t& y, U p, uint32_t pv, bool keep_min) {
+  if constexpr (PAIRS) {
+    const bool take = elem_less<PAIRS>(p, pv, x, y) == keep_min;
+    x = take ? p : x;
+    y = take ? pv : y;
+  } else {
+    x = keep_min ? umin_(x, p) : umax_(x, p);
+  }
+}
+
+// Sorts the m = R*T entries held as x[R], y[R] by T participating threads (t = thread
+// index within the group), ascending.  Entries are ord images (+ payloads), so bitwise
+// complement reverses their order: during merge phase k every entry whose index has
+// bit k set is kept complemented, which turns the descending half-merges of Batcher's
+// network into ascending ones and leaves every compare-exchange a plain min/max.
+// s_x / s_y: shared scratch of m entries, used only for exchanges between warps.
 template <bool PAIRS, int R, int T, class U>
 __device__ __forceinline__ void net_sort(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
   constexpr int M = R * T;
 #pragma unroll
   for (int k = 2; k <= M; k <<= 1) {
+    // Entering phase k: flip the entries whose complement state changes.
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int e = t * R + i;
+      const bool before = (k >= 4) && ((e & (k >> 1)) != 0);
+      const bool now = (k < M) && ((e & k) != 0);
+      const U m = (before != now) ? ~U(0) : U(0);
+      x[i] ^= m;
+      if constexpr (PAIRS) y[i] ^= (uint32_t)m;
+    }
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       if (j < R) {
         // Both entries of every pair are in this thread.
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          if ((i & j) == 0) {
-            const bool up = (k < R) ? ((i & k) == 0) : (((t * R) & k) == 0);
-            cx<PAIRS>(x[i], y[i], x[i | j], y[i | j], up);
-          }
-        }
+        for (int i = 0; i < R; ++i)
+          if ((i & j) == 0) cx_up<PAIRS>(x[i], y[i], x[i | j], y[i | j]);
       } else if (j < 32 * R) {
-        // Partner entry: same register of lane t ^ (j / R).
+        // Partner entry: same register of lane t ^ (j / R); the lower index keeps the min.
         const int d = j / R;
-        const bool keep_min = (((t & d) == 0) == (((t * R) & k) == 0));
+        const bool keep_min = (t & d) == 0;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           const U p = shfl_xor_any(x[i], d);
           const uint32_t pv = PAIRS ? __shfl_xor_sync(~0u, y[i], d) : 0u;
-          const bool take = elem_less<PAIRS>(p, pv, x[i], y[i]) == keep_min;
-          x[i] = take ? p : x[i];
-          if constexpr (PAIRS) y[i] = take ? pv : y[i];
+          keep_one<PAIRS>(x[i], y[i], p, pv, keep_min);
         }
       } else {
-        // Partner in another warp: exchange through shared memory.
+        // Partner in another warp: exchange rows through shared memory.
         const int d = j / R;
-        const bool keep_min = (((t & d) == 0) == (((t * R) & k) == 0));
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          s_x[t * R + i] = x[i];
-          if constexpr (PAIRS) s_y[t * R + i] = y[i];
-        }
+        const bool keep_min = (t & d) == 0;
+        store_row<R>(s_x + t * R, x);
+        if constexpr (PAIRS) store_row<R>(s_y + t * R, y);
         __syncthreads();
+        U p[R];
+        uint32_t pv[R];
+        load_row<R>(s_x + (t ^ d) * R, p);
+        if constexpr (PAIRS) load_row<R>(s_y + (t ^ d) * R, pv);
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const U p = s_x[(t ^ d) * R + i];
-          const uint32_t pv = PAIRS ? s_y[(t ^ d) * R + i] : 0u;
-          const bool take = elem_less<PAIRS>(p, pv, x[i], y[i]) == keep_min;
-          x[i] = take ? p : x[i];
-          if constexpr (PAIRS) y[i] = take ? pv : y[i];
-        }
+        for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
         __syncthreads();
       }
     }
@@ -103,7 +171,6 @@ template <class KT, bool PAIRS, int R, int T>
 __device__ __forceinline__ void sort_run(const Params& P, const Run& r, int t, typename KT::U* s_x,
                                          uint32_t* s_y, bool block_sync) {
   using U = typename KT::U;
-  constexpr int M = R * T;
   const U* src = (const U*)P.b.key[r.parity] + r.off;
   const uint32_t* vsrc = PAIRS ? P.b.val[r.parity] + r.off : nullptr;
   U* dst = (U*)P.b.final_key + r.off;
@@ -118,18 +185,12 @@ __device__ __forceinline__ void sort_run(const Params& P, const Run& r, int t, t
   if (block_sync) __syncthreads(); else __syncwarp();
   U x[R];
   uint32_t y[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    x[i] = s_x[t * R + i];
-    y[i] = PAIRS ? s_y[t * R + i] : 0u;
-  }
+  load_row<R>(s_x + t * R, x);
+  if constexpr (PAIRS) load_row<R>(s_y + t * R, y);
   if (block_sync) __syncthreads(); else __syncwarp();
   net_sort<PAIRS, R, T>(x, y, t, s_x, s_y);
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    s_x[t * R + i] = x[i];
-    if constexpr (PAIRS) s_y[t * R + i] = y[i];
-  }
+  store_row<R>(s_x + t * R, x);
+  if constexpr (PAIRS) store_row<R>(s_y + t * R, y);
   if (block_sync) __syncthreads(); else __syncwarp();
 #pragma unroll
   for (int i = 0; i < R; ++i) {
