@@ -107,6 +107,22 @@ int bqs_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int
                        bqs_stream_t stream);
 
 /*
+ * bqs_sort_batched -- the segmented sort for batches: like bqs_sort_segmented, but
+ * the caller states n = seg_offsets[nseg] (the total key count, used to size the
+ * scratch), so the call itself never reads device memory back.  When `stream` is
+ * being captured into a CUDA graph, the whole level loop is captured as a device-
+ * side loop (a conditional while node; each iteration is one level of persistent
+ * kernels over all segments), so one graph launch sorts the whole batch with no
+ * host involvement.  Outside capture it behaves like bqs_sort_segmented.  Errors
+ * found on the device inside a captured loop (decreasing offsets) stop the loop
+ * and are not reported back.  bqs_sort and bqs_sort_pairs capture the same way.
+ *   n             number of keys in the array, must equal seg_offsets[nseg].
+ *   seg_offsets   device, nseg+1 int64, non-decreasing, seg_offsets[0] >= 0.
+ */
+int bqs_sort_batched(void* keys, int64_t n, const int64_t* seg_offsets, int64_t nseg,
+                     int32_t dtype, bqs_stream_t stream);
+
+/*
  * bqs_sort_pairs -- sorts (keys[i], vals[i]) pairs in place, ordered
  * lexicographically by (key, payload), so the result is unique when payloads
  * are distinct.  Paper: the same method as bqs_sort applied to a wider element

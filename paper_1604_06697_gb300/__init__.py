@@ -100,6 +100,22 @@ def sort_segmented(keys, seg_offsets, stream=None):
     return keys
 
 
+def sort_batched(keys, seg_offsets, stream=None):
+    """Segmented sort that never reads device memory back during the call.
+
+    Inside ``torch.cuda.graph(...)`` capture the whole level loop is recorded as a
+    device-side loop, so replaying the graph sorts the batch in one launch.
+    """
+    import torch
+    _require_cuda(keys, seg_offsets)
+    if seg_offsets.dtype != torch.int64:
+        raise TypeError("seg_offsets must be int64")
+    _check(_native.lib().bqs_sort_batched(keys.data_ptr(), keys.numel(), seg_offsets.data_ptr(),
+                                          seg_offsets.numel() - 1, _dtype_code(keys),
+                                          _stream_ptr(keys, stream)), "bqs_sort_batched")
+    return keys
+
+
 def partition(keys, pivot, out=None, stream=None):
     """Partitions ``keys`` around ``pivot`` into ``out``; returns (out, split).
 

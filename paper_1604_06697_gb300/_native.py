@@ -35,6 +35,7 @@ SIGNATURES = {
     "bqs_partition": (ctypes.c_int, [c_vp, c_i64, ctypes.POINTER(Pivot), c_vp, ctypes.POINTER(c_i64), c_vp]),
     "bqs_sort": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp]),
     "bqs_sort_segmented": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_vp]),
+    "bqs_sort_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_i32, c_vp]),
     "bqs_sort_pairs": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_vp]),
     "bqs_sort_noalloc": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp]),
     "bqs_set_option": (ctypes.c_int, [c_i32, c_i64]),

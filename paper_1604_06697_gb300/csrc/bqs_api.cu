@@ -157,6 +157,24 @@ int bqs_sort_segmented(void* keys, const int64_t* seg_offsets, int64_t nseg, int
   return dispatch(dtype, c);
 }
 
+int bqs_sort_batched(void* keys, int64_t n, const int64_t* seg_offsets, int64_t nseg,
+                     int32_t dtype, bqs_stream_t stream) {
+  if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || nseg < 0 || n < 0 || n > kMaxN)
+    return BQS_ERR_INVALID;
+  t_stats = Stats{};
+  if (nseg == 0 || n == 0) return BQS_OK;
+  if (!seg_offsets || ((uintptr_t)seg_offsets & 7u)) return BQS_ERR_INVALID;
+  if (!keys || !aligned16(keys)) return BQS_ERR_INVALID;
+  Call c;
+  c.keys = keys;
+  c.n = n;
+  c.seg_offsets = seg_offsets;
+  c.nseg = nseg;
+  c.stream = stream;
+  c.opt = snapshot_options();
+  return dispatch(dtype, c);
+}
+
 int bqs_partition(const void* keys, int64_t n, const bqs_pivot* pivot, void* out, int64_t* split,
                   bqs_stream_t stream) {
   if (!pivot || !split || pivot->reserved != 0) return BQS_ERR_INVALID;

@@ -99,7 +99,7 @@ struct ListCounts {
 struct Ctrl {
   ListCounts lists[2];
   int status;
-  int pad;
+  int level;          // current level when the level loop runs on the device
   unsigned long long moved_keys;
   unsigned long long equal_keys;
   unsigned long long small_segs;
@@ -138,9 +138,15 @@ struct Params {
   int depth_limit;    // partition levels before the depth fallback pivot
   int route_children; // 0: a single partition step (no recursion)
   int tile;           // keys per partition tile (for tile counts)
-  int pad;
+  int device_loop;    // 1: the level (and its parity) is read from ctrl->level
   int64_t n_keys;     // length of the key arrays
 };
+
+// Parity of the lists the current level consumes: given by the host when it drives
+// the level loop, read from the control block when the loop runs on the device.
+__device__ __forceinline__ int level_parity(const Params& P, int host_p) {
+  return P.device_loop ? (*(volatile int*)&P.ctrl->level & 1) : host_p;
+}
 
 // Tiles of a segment start at its first key rounded down to a 16-byte group (4 keys):
 // tile k covers [tile_origin(off) + k*tile, + tile) clipped to the segment, so only the

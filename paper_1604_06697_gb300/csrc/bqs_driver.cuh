@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bqs_graph.cuh"
 #include "bqs_internal.h"
 #include "bqs_kernels.cuh"
 #include "bqs_local.cuh"
@@ -219,6 +220,64 @@ inline int status_code(int device_status) {
     if (e_ != cudaSuccess) return fail_cuda(e_, #call);           \
   } while (0)
 
+// A non-blocking stream of the calling thread, used only to record the body of the
+// device-side level loop into the conditional node's graph.
+inline cudaStream_t helper_stream() {
+  static thread_local cudaStream_t hs = nullptr;
+  if (!hs && cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    hs = nullptr;
+  }
+  return hs;
+}
+
+// Adds to the graph being captured on `s` a conditional while node whose body is one
+// level of the sort, recorded on a helper stream with fixed (persistent) grids; the
+// kernels read the level parity and the work counts from the control block, and
+// k_level_end sets the loop condition.
+template <class KT, bool PAIRS>
+int capture_level_loop(const Params& P, const Variant& var, cudaStream_t s, int max_levels,
+                       bool local_on) {
+  cudaStreamCaptureStatus cs;
+  unsigned long long id = 0;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t nd = 0;
+  BQS_CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &edata, &nd));
+  cudaGraphConditionalHandle h;
+  BQS_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  BQS_CK(cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  BQS_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+
+  cudaStream_t hs = helper_stream();
+  if (!hs) return kErrCuda;
+  BQS_CK(cudaStreamBeginCaptureToGraph(hs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const int sms = sm_count();
+  k_level_begin<<<1, 32, 0, hs>>>(P);
+  k_pivot<KT, PAIRS><<<8 * sms, 256, 0, hs>>>(P);
+  var.launch(P, persistent_grid(var.fn, var.threads, var.smem), hs);
+  k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, hs>>>(P);
+  k_fill<KT, PAIRS><<<4 * sms, 256, 0, hs>>>(P, 0);
+  if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), hs);
+  k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, hs>>>(P, 0);
+  k_small_block<KT, PAIRS><<<16 * sms, 256, 0, hs>>>(P, 0);
+  k_level_end<<<1, 32, 0, hs>>>(P, h, max_levels);
+  const cudaError_t launch_err = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  const cudaError_t end_err = cudaStreamEndCapture(hs, &captured);
+  if (launch_err != cudaSuccess) return fail_cuda(launch_err, "recording the level loop");
+  if (end_err != cudaSuccess) return fail_cuda(end_err, "cudaStreamEndCapture(level loop body)");
+  return kOk;
+}
+
 template <class KT, bool PAIRS>
 int run_call(const Call& c, Stats& st) {
   using U = typename KT::U;
@@ -280,13 +339,34 @@ int run_call(const Call& c, Stats& st) {
     P.depth_limit = c.opt.depth_limit >= 0 ? (int)c.opt.depth_limit : 2 * lg + 3;
   }
 
+  // On a stream that is being captured into a CUDA graph the level loop runs on the
+  // device (nothing can be read back while capturing).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  BQS_CK(cudaStreamIsCapturing(s, &cap));
+  const bool device_loop = cap == cudaStreamCaptureStatusActive && !c.fixed_ws;
+  if (device_loop && c.partition_only) return kErrUnsupported;   // split is read back
+  if (!device_loop && !c.fixed_ws) helper_stream();   // created outside any capture
+
   static thread_local Ctrl pageable_ctrl;
-  Ctrl* host = c.fixed_ws ? &pageable_ctrl : pinned_ctrl();
-  const bool timing = c.opt.timing && !c.fixed_ws;
+  Ctrl* host = (c.fixed_ws || device_loop) ? &pageable_ctrl : pinned_ctrl();
+  const bool timing = c.opt.timing && !c.fixed_ws && !device_loop;
   BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
 
   ListCounts cur{};
-  if (c.partition_only) {
+  if (device_loop) {
+    if (c.seg_offsets) {
+      const int g = (int)std::min<int64_t>((c.nseg + 255) / 256, 4 * sm_count());
+      k_init_segments<KT, PAIRS><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
+    } else {
+      k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
+    }
+    BQS_CK(cudaGetLastError());
+    const int max_levels = P.depth_limit + 8 * (int)sizeof(U) + 40;
+    P.device_loop = 1;
+    P.p = 0;
+    st.kernel_launches += 10;   // per level
+    return capture_level_loop<KT, PAIRS>(P, var, s, max_levels, local_cutoff > small_cutoff);
+  } else if (c.partition_only) {
     k_init_partition<KT><<<1, 32, 0, s>>>(P, c.n, c.pivot_raw);
     st.kernel_launches += 1;
     cur.large = 1ull | ((unsigned long long)((c.n - 1) / tile + 1) << 32);

@@ -278,10 +278,11 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   __shared__ U s_red[2][8];
   __shared__ uint32_t s_redv[2][8];
 
-  const unsigned int count = min(P.ctrl->lists[P.p].todo, P.l.cap_large);
-  Seg* segs = P.l.large[P.p];
+  const int pp = level_parity(P, P.p);
+  const unsigned int count = min(P.ctrl->lists[pp].todo, P.l.cap_large);
+  Seg* segs = P.l.large[pp];
   for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
-    const unsigned int s = P.l.todo[P.p][i];
+    const unsigned int s = P.l.todo[pp][i];
     const Seg sg = segs[s];
     const U* keys = (const U*)P.b.key[sg.parity];
     const uint32_t* vals = P.b.val[sg.parity];
@@ -390,10 +391,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition(Params P) {
   __shared__ uint32_t s_tseg[THREADS];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long lc = P.ctrl->lists[P.p].large;
+  const int pp = level_parity(P, P.p);
+  const unsigned long long lc = P.ctrl->lists[pp].large;
   const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
-  const Seg* __restrict__ segs = P.l.large[P.p];
-  unsigned long long* cursor = P.l.cursor[P.p];
+  const Seg* __restrict__ segs = P.l.large[pp];
+  unsigned long long* cursor = P.l.cursor[pp];
 
   for (uint32_t round = 0;; ++round) {
     // Segment of each of this block's next THREADS tiles, one binary search per thread.
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition(Params P) {
 
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_bookkeep(Params P) {
-  const int p = P.p, q = p ^ 1;
+  const int p = level_parity(P, P.p), q = p ^ 1;
   const int lane = threadIdx.x & 31;
   const unsigned int count = min((unsigned int)P.ctrl->lists[p].large, P.l.cap_large);
   const unsigned int stride = gridDim.x * blockDim.x;
@@ -604,6 +606,7 @@ template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_fill(Params P, int p) {
   using U = typename KT::U;
   __shared__ uint32_t s_f;
+  p = level_parity(P, p);
   const unsigned long long lc = P.ctrl->lists[p].fill;
   const uint32_t count = min((uint32_t)lc, P.l.cap_fill), tiles = (uint32_t)(lc >> 32);
   const Fill* fills = P.l.fill[p];

@@ -80,6 +80,7 @@ __device__ __forceinline__ uint32_t pack_leaf(int begin, int len, int buf) {
 template <class KT, bool PAIRS, int L, int T>
 __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
   using U = typename KT::U;
+  p = level_parity(P, p);
   using S = LocalShape<KT, PAIRS, L>;
   using E = Elem<KT, PAIRS>;
   constexpr int WARPS = T / 32;

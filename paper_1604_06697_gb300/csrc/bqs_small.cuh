@@ -207,6 +207,7 @@ __device__ __forceinline__ void sort_run(const Params& P, const Run& r, int t, t
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_small_warp(Params P, int p) {
   using U = typename KT::U;
+  p = level_parity(P, p);
   __shared__ __align__(16) U s_x[8][kWarpSortMax];
   __shared__ __align__(16) uint32_t s_y[8][PAIRS ? kWarpSortMax : 1];
   const unsigned int count = min(P.ctrl->lists[p].tiny, P.l.cap_run);
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(256) k_small_warp(Params P, int p) {
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_small_block(Params P, int p) {
   using U = typename KT::U;
+  p = level_parity(P, p);
   __shared__ __align__(16) U s_x[kMaxSmall];
   __shared__ __align__(16) uint32_t s_y[PAIRS ? kMaxSmall : 1];
   const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);

@@ -134,10 +134,11 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned long long lc = P.ctrl->lists[P.p].large;
+  const int pp = level_parity(P, P.p);
+  const unsigned long long lc = P.ctrl->lists[pp].large;
   const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
-  const Seg* __restrict__ segs = P.l.large[P.p];
-  unsigned long long* cursor = P.l.cursor[P.p];
+  const Seg* __restrict__ segs = P.l.large[pp];
+  unsigned long long* cursor = P.l.cursor[pp];
   const int64_t n_total = P.n_keys;
 
   // Contiguous tile range of this block.
