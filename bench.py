@@ -48,6 +48,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="sort", choices=["sort", "pairs", "batched", "serving"],
+                    help="sort (the default headline line), pairs, batched or serving")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-tune", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -232,6 +236,10 @@ def run_ours(a):
 
     n = 1 << a.log2n
     bqs.set_option("pivot", 1 if a.pivot == "sqrt" else 0)
+    tuned = None
+    if not a.no_tune:   # launch shape chosen by the autotuner (cached per GPU/dtype/size)
+        from paper_1604_06697_gb300 import autotune
+        tuned = autotune.tune(a.dtype, n, kind="sort")["config"]
     host = inputs.make_keys(n, a.dtype, a.dist, a.seed)
     src = torch.from_numpy(host).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -346,7 +354,8 @@ def run_ours(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": a.dtype, "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "dist": a.dist, "seed": a.seed,
-                       "pivot": a.pivot, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "pivot": a.pivot, "autotuned": tuned,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (one resident 2^%d-key copy per step)" % a.log2n},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "levels_per_sort": levels[0] if levels else None,
@@ -358,10 +367,173 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ---- further workloads (one JSON line each) ---------------------------------------------------
+
+def _cuda_ms(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_pairs(a):
+    """2^26 (int64 key in [0, 2^20), uint32 payload = index) pairs, ordered by (key, payload)."""
+    import torch
+
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import inputs
+
+    n = 1 << 26
+    keys, vals = inputs.make_pairs(n, seed=1)
+    sk = torch.from_numpy(keys).cuda()
+    sv = torch.from_numpy(vals.view(np.int32)).cuda()
+    bqs.set_option("pivot", 1)
+    bqs.set_option("local_cutoff", -1)
+    wk, wv = torch.empty_like(sk), torch.empty_like(sv)
+    for _ in range(a.warmup):
+        wk.copy_(sk); wv.copy_(sv); bqs.sort_pairs(wk, wv)
+    bufs = [(sk.clone(), sv.clone()) for _ in range(a.steps)]
+    bqs.set_option("timing", 1)
+    pm = pb = 0.0
+    launches = 0
+
+    def steps():
+        nonlocal pm, pb, launches
+        for k, v in bufs:
+            bqs.sort_pairs(k, v)
+            s = bqs.stats()
+            pm += s["partition_ms"]; pb += s["partition_bytes"]; launches += s["kernel_launches"]
+    ms = _cuda_ms(steps)
+    bqs.set_option("timing", 0)
+    k0 = bufs[0][0]
+    ok = bool(((k0[1:] > k0[:-1]) | ((k0[1:] == k0[:-1]) & (bufs[0][1][1:] > bufs[0][1][:-1]))).all())
+    peak, kind = measured_peak_gbs()
+    ach = pb / (pm / 1e3) / 1e9 if pm else None
+    print(json.dumps({
+        "workload": "pairs", "metric": "key-value pairs/s", "value": n * a.steps / (ms / 1e3),
+        "unit": "pairs/s", "ms_per_step": ms / a.steps, "steps": a.steps, "warmup": a.warmup,
+        "dtype": "int64+u32", "data": "synthetic",
+        "config": {"workload": "bqs_sort_pairs 2^26 int64 keys mod 2^20, payload = index, seed 1",
+                   "pivot": "sqrt", "local_cutoff": -1},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak if ach else None, "kernel": "k_partition_tma (pairs)"},
+        "gpu_launches": launches, "ordered_check": ok}), flush=True)
+
+
+def run_batched(a):
+    """65,536 int32 arrays, lengths log-uniform in [16, 65536], one graph launch (the
+    device-side level loop) against one bqs_sort call per array."""
+    import torch
+
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import autotune, inputs
+
+    nseg = 65536
+    keys, off = inputs.make_segments(nseg, seed=2)
+    n = int(off[-1])
+    src = torch.from_numpy(keys).cuda()
+    toff = torch.from_numpy(off).cuda()
+    bqs.set_option("pivot", 1)
+    tuned = autotune.tune("int32", n, kind="batched", nseg=nseg)
+
+    scratch = src.clone()
+    bqs.sort_batched(scratch, toff)      # one-time set-up outside capture
+    torch.cuda.synchronize()
+    del scratch
+    bufs = [src.clone() for _ in range(a.steps)]
+    graphs = []
+    cap = torch.cuda.Stream()
+    for b in bufs:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            bqs.sort_batched(b, toff)
+        graphs.append(g)
+    warm = src.clone()
+    gw = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gw, stream=cap):
+        bqs.sort_batched(warm, toff)
+    for _ in range(a.warmup):
+        warm.copy_(src)
+        gw.replay()
+    ms = _cuda_ms(lambda: [g.replay() for g in graphs])
+    out = bufs[0].cpu().numpy()
+    ok = all(np.array_equal(out[off[i]:off[i + 1]], np.sort(keys[off[i]:off[i + 1]]))
+             for i in range(0, nseg, 997))
+
+    # Baseline: one bqs_sort call per array (arrays placed at 16-byte aligned offsets).
+    lens = np.diff(off)
+    poff = np.zeros(nseg + 1, np.int64)
+    np.cumsum((lens + 3) // 4 * 4, out=poff[1:])
+    padded = np.zeros(int(poff[-1]), np.int32)
+    for i in range(nseg):
+        padded[poff[i]:poff[i] + lens[i]] = keys[off[i]:off[i + 1]]
+    pbuf = torch.from_numpy(padded).cuda()
+    views = [pbuf[int(poff[i]):int(poff[i] + lens[i])] for i in range(nseg)]
+    for v in views[:64]:
+        bqs.sort(v)
+    pbuf.copy_(torch.from_numpy(padded).cuda())
+    base_ms = _cuda_ms(lambda: [bqs.sort(v) for v in views])
+    print(json.dumps({
+        "workload": "batched", "metric": "keys/s, 65,536 int32 arrays in one graph launch",
+        "value": n * a.steps / (ms / 1e3), "unit": "keys/s", "ms_per_step": ms / a.steps,
+        "steps": a.steps, "warmup": a.warmup, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "bqs_sort_batched, 65,536 arrays, lengths floor(exp(U(ln16, ln65536))), seed 2",
+                   "total_keys": n, "autotuned": tuned["config"], "pivot": "sqrt"},
+        "baseline_one_call_per_array": {"value": n / (base_ms / 1e3), "unit": "keys/s",
+                                        "ms": base_ms, "calls": nseg},
+        "speedup_vs_per_array": base_ms / (ms / a.steps), "sorted_check": ok}), flush=True)
+
+
+def run_serving(a):
+    """Poisson sort requests (sizes 2^U(10,26), mixed dtypes) at several rates, served
+    with continuous batching and with one launch per request."""
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import serving
+
+    bqs.set_option("pivot", 1)
+    bqs.set_option("local_cutoff", -1)
+    pool = serving.KeyPool(max_size=1 << 26, seed=3)
+    rows = []
+    for rate in (1000, 2000, 5000, 10000, 20000):
+        row = {"rate_hz": rate}
+        for mode in ("plain", "batched"):
+            reqs = serving.make_requests(a.serve_requests, rate, seed=3)
+            offered = sum(r.size for r in reqs) / max(r.arrival for r in reqs)
+            rep = serving.ServingLoop(pool, mode=mode, slots=3, hbm_budget=64 << 30,
+                                      max_batch_keys=1 << 27).run(reqs)
+            row[mode] = {k: rep[k] for k in ("p50_ms", "p99_ms", "served_keys_per_s",
+                                             "batches", "hbm_peak_bytes")}
+            row["offered_keys_per_s"] = offered
+        rows.append(row)
+    print(json.dumps({
+        "workload": "serving", "metric": "p50/p99 latency and served keys/s, batched vs plain",
+        "unit": "ms / keys/s", "requests_per_rate": a.serve_requests, "data": "synthetic",
+        "config": {"sizes": "floor(2^U(10,26))", "dtypes": "uniform over int32/int64/float64",
+                   "arrivals": "Poisson", "hbm_budget_bytes": 64 << 30, "slots": 3, "seed": 3},
+        "rates": rows}), flush=True)
+
+
 def main(argv=None):
     a = parse_args(argv)
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "pairs":
+        run_pairs(a)
+    elif a.workload == "batched":
+        run_batched(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_ours(a)
 

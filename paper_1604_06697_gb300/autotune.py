@@ -1,0 +1,134 @@
+"""Autotuner for the sort's launch shape.
+
+Chooses, for one workload class (dtype, size bucket, single array or batch), the
+partition tile variant (threads x keys per thread), the small-segment cutoff and
+the single-block local-sort cutoff by timing every candidate on a synthetic input
+of that class with CUDA events.  Results are cached in a JSON file keyed by GPU
+name, dtype, workload kind and log2 size bucket, so a later process applies the
+choice without re-timing.  The tuner only sets the library's options; every
+candidate runs the same kernels through the C ABI.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+from . import inputs
+
+TILES = (0, 1, 2)              # TMA partition variants (see bqs_set_option(BQS_OPT_TILE))
+SMALL_CUTOFFS = (256, 1024, 2048)
+LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(base, "paper_1604_06697_gb300", "autotune.json")
+
+
+def cache_key(dtype: str, n: int, kind: str) -> str:
+    import torch
+    gpu = torch.cuda.get_device_name()
+    return f"{gpu}|{dtype}|{kind}|2^{max(0, int(math.log2(max(1, n))))}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(path, table):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(config: dict) -> None:
+    import paper_1604_06697_gb300 as bqs
+    for k in ("tile", "small_cutoff", "local_cutoff"):
+        if k in config:
+            bqs.set_option(k, int(config[k]))
+
+
+def _time(run, reps: int) -> float:
+    import torch
+    ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return min(ms)
+
+
+def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
+         cache_path: str | None = None, force: bool = False, candidates=None) -> dict:
+    """Returns (and caches) the fastest configuration for this workload class.
+
+    kind: "sort" (one array of n keys, uniform values) or "batched" (nseg arrays with
+    log-uniform lengths in [16, 65536] totalling about n keys, sorted by
+    bqs_sort_batched).
+    """
+    import torch
+
+    import paper_1604_06697_gb300 as bqs
+
+    path = cache_path or default_cache_path()
+    table = _load(path)
+    key = cache_key(dtype, n, kind)
+    if key in table and not force:
+        apply(table[key]["config"])
+        return table[key]
+
+    if kind == "batched":
+        keys, off = inputs.make_segments(nseg, seed=2, dtype=dtype)
+        src = torch.from_numpy(keys).cuda()
+        toff = torch.from_numpy(off).cuda()
+        work = torch.empty_like(src)
+
+        def run():
+            bqs.sort_batched(work, toff)
+
+        def prep():
+            work.copy_(src)
+    else:
+        src = torch.from_numpy(inputs.make_keys(n, dtype, "uniform", 1)).cuda()
+        work = torch.empty_like(src)
+
+        def run():
+            bqs.sort(work)
+
+        def prep():
+            work.copy_(src)
+
+    saved = {k: bqs.get_option(k) for k in ("tile", "small_cutoff", "local_cutoff")}
+    results = []
+    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l)
+                           for t, s, l in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS)]
+    try:
+        for cfg in cands:
+            apply(cfg)
+            best = float("inf")
+            for _ in range(reps):
+                prep()
+                torch.cuda.synchronize()
+                best = min(best, _time(run, 1))
+            results.append((best, cfg))
+    finally:
+        apply(saved)
+    results.sort(key=lambda r: r[0])
+    entry = {"config": results[0][1], "ms": results[0][0],
+             "timed": [{"config": c, "ms": t} for t, c in results]}
+    table[key] = entry
+    _store(path, table)
+    apply(entry["config"])
+    return entry
