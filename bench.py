@@ -48,8 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="sort", choices=["sort", "pairs", "batched", "serving"],
-                    help="sort (the default headline line), pairs, batched or serving")
+    ap.add_argument("--workload", default="sort",
+                    choices=["sort", "pairs", "batched", "serving", "matrix"],
+                    help="sort (the default headline line), pairs, batched, serving or matrix")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-tune", action="store_true")
     return ap.parse_args(argv)
@@ -493,6 +494,48 @@ def run_batched(a):
         "speedup_vs_per_array": base_ms / (ms / a.steps), "sorted_check": ok}), flush=True)
 
 
+def run_matrix(a):
+    """2^24 and 2^28 keys x int32/int64/float64 x the six distributions (seed 1)."""
+    import torch
+
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import autotune, inputs
+
+    bqs.set_option("pivot", 1)
+    rows = []
+    peak, _ = measured_peak_gbs()
+    for log2n in (24, 28):
+        n = 1 << log2n
+        for dtype in ("int32", "int64", "float64"):
+            autotune.tune(dtype, n, kind="sort")
+            for dist in inputs.DISTRIBUTIONS:
+                src = torch.from_numpy(inputs.make_keys(n, dtype, dist, 1)).cuda()
+                work = torch.empty_like(src)
+                for _ in range(a.warmup):
+                    work.copy_(src)
+                    bqs.sort(work)
+                best, pm, pb, lv = float("inf"), 0.0, 0.0, 0
+                bqs.set_option("timing", 1)
+                for _ in range(a.steps):
+                    work.copy_(src)
+                    ms = _cuda_ms(lambda: bqs.sort(work))
+                    s = bqs.stats()
+                    if ms < best:
+                        best, pm, pb, lv = ms, s["partition_ms"], s["partition_bytes"], s["levels"]
+                bqs.set_option("timing", 0)
+                ach = pb / (pm / 1e3) / 1e9 if pm else None
+                rows.append({"log2n": log2n, "dtype": dtype, "dist": dist, "ms": round(best, 3),
+                             "keys_per_s": n / (best / 1e3), "levels": lv,
+                             "partition_GBs": ach, "partition_frac": ach / peak if ach else None})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                del src, work
+    print(json.dumps({"workload": "matrix", "metric": "keys/s per size x dtype x distribution",
+                      "unit": "keys/s", "timing": f"best of {a.steps} sorts after {a.warmup} warm-up",
+                      "data": "synthetic", "rows": rows}), flush=True)
+
+
 def run_serving(a):
     """Poisson sort requests (sizes 2^U(10,26), mixed dtypes) at several rates, served
     with continuous batching and with one launch per request."""
@@ -534,6 +577,8 @@ def main(argv=None):
         run_batched(a)
     elif a.workload == "serving":
         run_serving(a)
+    elif a.workload == "matrix":
+        run_matrix(a)
     else:
         run_ours(a)
 

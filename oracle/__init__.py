@@ -54,6 +54,8 @@ def _load():
         lib.oracle_block_partition.restype = i64
         lib.oracle_partition_by_value.argtypes = [vp, i64, i32, vp, vp]
         lib.oracle_partition_by_value.restype = i64
+        lib.oracle_select.argtypes = [vp, i64, i32, i64, vp]
+        lib.oracle_select.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -66,7 +68,7 @@ def use_library(path: str) -> None:
     _load()  # make sure the signatures of the default build are known
     lib = ctypes.CDLL(path)
     for name in ("oracle_sort", "oracle_sort_pairs", "oracle_sort_segmented",
-                 "oracle_block_partition", "oracle_partition_by_value"):
+                 "oracle_block_partition", "oracle_partition_by_value", "oracle_select"):
         f, g = getattr(lib, name), getattr(_lib, name)
         f.argtypes, f.restype = g.argtypes, g.restype
     _lib = lib
@@ -160,6 +162,15 @@ def partition_by_value(keys: np.ndarray, pivot):
     if s < 0:
         raise ValueError("oracle_partition_by_value: invalid arguments")
     return out, int(s)
+
+
+def select(keys: np.ndarray, k: int):
+    """The key at position k of the sorted keys (k-th order statistic)."""
+    a = np.ascontiguousarray(keys)
+    out = np.zeros(1, dtype=a.dtype)
+    if _load().oracle_select(_ptr(a), a.size, _dtype_code(a), int(k), _ptr(out)):
+        raise ValueError("oracle_select: invalid arguments")
+    return out[0]
 
 
 def ord_f64(x: np.ndarray) -> np.ndarray:

@@ -443,6 +443,35 @@ int64_t oracle_block_partition(void* keys, int64_t n, int32_t dtype, int64_t piv
   return p;
 }
 
+// The key that a sorted copy of keys[0, n) holds at position k (the k-th order statistic,
+// which is the definition of that output position), written to *out.  Used to check
+// sampled positions of sorts too large for oracle_sort.  The selection step is the
+// library's std::nth_element on a copy, with the same total order as the sort.
+int oracle_select(const void* keys, int64_t n, int32_t dtype, int64_t k, void* out) {
+  if (n < 1 || !keys || !out || k < 0 || k >= n) return -1;
+  switch (dtype) {
+    case 0: {
+      std::vector<int32_t> a((const int32_t*)keys, (const int32_t*)keys + n);
+      std::nth_element(a.begin(), a.begin() + k, a.end(), LessI32());
+      *(int32_t*)out = a[k];
+      return 0;
+    }
+    case 1: {
+      std::vector<int64_t> a((const int64_t*)keys, (const int64_t*)keys + n);
+      std::nth_element(a.begin(), a.begin() + k, a.end(), LessI64());
+      *(int64_t*)out = a[k];
+      return 0;
+    }
+    case 2: {
+      std::vector<double> a((const double*)keys, (const double*)keys + n);
+      std::nth_element(a.begin(), a.begin() + k, a.end(), LessF64());
+      *(double*)out = a[k];
+      return 0;
+    }
+    default: return -1;
+  }
+}
+
 // Plain stable value partition (the definition behind bqs_partition).  pivot points to
 // one key of the given dtype.  Returns count(< pivot), or -1 on invalid arguments.
 int64_t oracle_partition_by_value(const void* keys, int64_t n, int32_t dtype, const void* pivot,

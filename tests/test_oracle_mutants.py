@@ -44,6 +44,7 @@ MUTANTS = [
      "size_t mid = (pos.size() - 1) / 4;"),
     ("depth limit", "2 * floor_log2(n) + 3", "2 * floor_log2(n) + 300"),
     ("value partition", "else out[hi++] = keys[i];", "else out[hi++] = pivot;"),
+    ("order statistic index", "*(int32_t*)out = a[k];", "*(int32_t*)out = a[k > 0 ? k - 1 : k];"),
 ]
 
 _RUNNER = r"""
@@ -69,6 +70,7 @@ pins = [
     lambda: P.test_partition_by_value_definition("int32"),
     lambda: P.test_block_partition_large_and_compares_each_element_once(),
     lambda: P.test_default_depth_limit_is_the_papers(1 << 10),
+    lambda: P.test_select_is_the_order_statistic("int32"),
 ]
 for i, pin in enumerate(pins):
     try:

@@ -269,6 +269,22 @@ def test_partition_by_value_definition(dtype):
             assert np.array_equal(out[:s], a[a < pv]) and np.array_equal(out[s:], a[a >= pv])
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_select_is_the_order_statistic(dtype):
+    # v is the k-th order statistic iff count(x < v) <= k < count(x <= v) (under the
+    # total order; for float64 ord() makes -0.0 < +0.0).
+    for n in (1, 2, 7, 100, 1001):
+        a = (inputs.splitmix64(n, n) % np.uint64(13)).astype(dtype)
+        if dtype == "float64":
+            a = np.where(a == 0, np.float64(-0.0), a)
+            a[: n // 3] = 0.0
+        key = oracle.ord_f64(a) if dtype == "float64" else a
+        for k in range(n):
+            v = oracle.select(a, k)
+            kv = oracle.ord_f64(np.array([v]))[0] if dtype == "float64" else v
+            assert int(np.count_nonzero(key < kv)) <= k < int(np.count_nonzero(key <= kv))
+
+
 def test_segmented_is_per_segment_sort():
     keys, off = inputs.make_segments(64, seed=2, lo=16, hi=4096)
     got = oracle.sort_segmented(keys, off)
