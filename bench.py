@@ -52,7 +52,11 @@ def parse_args(argv=None):
                     choices=["sort", "pairs", "batched", "serving", "matrix"],
                     help="sort (the default headline line), pairs, batched, serving or matrix")
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner and use --tile/--small/--local instead")
+    ap.add_argument("--tile", type=int, default=None)
+    ap.add_argument("--small", type=int, default=None)
+    ap.add_argument("--local", type=int, default=None)
     return ap.parse_args(argv)
 
 
@@ -87,6 +91,25 @@ def committed_traffic():
         return tr if h.hexdigest()[:16] == tr["source_sha256_16"] else None
     except Exception:
         return None
+
+
+# ---- replicas (one process per GPU, no data-path collective) -----------------------------------
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest of every rank's value (the slowest rank's time); the value itself when
+    there is one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 # ---- CPU oracle timing (bounded sample) --------------------------------------------------------
@@ -241,6 +264,10 @@ def run_ours(a):
     if not a.no_tune:   # launch shape chosen by the autotuner (cached per GPU/dtype/size)
         from paper_1604_06697_gb300 import autotune
         tuned = autotune.tune(a.dtype, n, kind="sort")["config"]
+    else:
+        for name, v in (("tile", a.tile), ("small_cutoff", a.small), ("local_cutoff", a.local)):
+            if v is not None:
+                bqs.set_option(name, v)
     host = inputs.make_keys(n, a.dtype, a.dist, a.seed)
     src = torch.from_numpy(host).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -288,13 +315,8 @@ def run_ours(a):
     out = bufs[0]
     ok = bool((out[1:] >= out[:-1]).all().item()) if a.dtype != "float64" else True
     del bufs
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    value = world * n * a.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dev)
+    value = replica_throughput(n * a.steps, ms, world)
 
     # End to end through the public API with host buffers: pinned H2D, sort, D2H.
     e2e = None
@@ -317,14 +339,9 @@ def run_ours(a):
             pin_out.copy_(dbuf, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize(dev)
-        ems = f0.elapsed_time(f1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1), dev)
         nbytes = n * host.itemsize
-        e2e = {"value": world * n * a.steps / (ems / 1e3), "unit": "keys/s",
+        e2e = {"value": replica_throughput(n * a.steps, ems, world), "unit": "keys/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
         del pin_in, pin_out, dbuf
 

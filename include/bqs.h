@@ -162,8 +162,14 @@ typedef enum {
   BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
   BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */
   BQS_OPT_TILE = 4,         /* partition tile variant: 0 = default, 1..N autotuner choices */
-  BQS_OPT_LOCAL_CUTOFF = 5  /* segments up to this size are sorted inside one thread block
+  BQS_OPT_LOCAL_CUTOFF = 5, /* segments up to this size are sorted inside one thread block
                                (-1 = as large as one block holds; 0 = off, the default) */
+  BQS_OPT_WAIT_LIMIT = 6,   /* polls before a bounded device-side wait gives up and the
+                               call returns BQS_ERR_TIMEOUT (default 2^26, seconds) */
+  BQS_OPT_TEST_STALL = 7    /* failure-path testing: 1 makes the first partition launch
+                               of a sort leave one tile unrequested, so its bounded wait
+                               runs out (the call returns BQS_ERR_TIMEOUT, the device
+                               stays usable; the keys are then unspecified) */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

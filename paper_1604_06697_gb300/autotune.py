@@ -17,7 +17,7 @@ import os
 
 from . import inputs
 
-TILES = (0, 1, 2)              # TMA partition variants (see bqs_set_option(BQS_OPT_TILE))
+TILES = (0, 1, 2, 3, 4, 5)     # TMA partition variants (see bqs_set_option(BQS_OPT_TILE))
 SMALL_CUTOFFS = (256, 1024, 2048)
 LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
 

@@ -222,12 +222,20 @@ int bqs_set_option(int32_t opt, int64_t value) {
       g_opt.timing = value;
       return BQS_OK;
     case BQS_OPT_TILE:
-      if (value < 0 || value > 3) return BQS_ERR_INVALID;  // the four variants() entries
+      if (value < 0 || value > 5) return BQS_ERR_INVALID;  // the six variants() entries
       g_opt.tile_variant = value;
       return BQS_OK;
     case BQS_OPT_LOCAL_CUTOFF:
       if (value < -1 || value > (1 << 20)) return BQS_ERR_INVALID;
       g_opt.local_cutoff = value;
+      return BQS_OK;
+    case BQS_OPT_WAIT_LIMIT:
+      if (value < 1 || value > 0xFFFFFFFFll) return BQS_ERR_INVALID;
+      g_opt.wait_limit = value;
+      return BQS_OK;
+    case BQS_OPT_TEST_STALL:
+      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      g_opt.test_stall = value;
       return BQS_OK;
     default:
       return BQS_ERR_UNSUPPORTED;
@@ -244,6 +252,8 @@ int bqs_get_option(int32_t opt, int64_t* value) {
     case BQS_OPT_TIMING: *value = g_opt.timing; return BQS_OK;
     case BQS_OPT_TILE: *value = g_opt.tile_variant; return BQS_OK;
     case BQS_OPT_LOCAL_CUTOFF: *value = g_opt.local_cutoff; return BQS_OK;
+    case BQS_OPT_WAIT_LIMIT: *value = g_opt.wait_limit; return BQS_OK;
+    case BQS_OPT_TEST_STALL: *value = g_opt.test_stall; return BQS_OK;
     default: return BQS_ERR_UNSUPPORTED;
   }
 }

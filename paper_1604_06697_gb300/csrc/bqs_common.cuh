@@ -140,6 +140,8 @@ struct Params {
   int tile;           // keys per partition tile (for tile counts)
   int device_loop;    // 1: the level (and its parity) is read from ctrl->level
   int64_t n_keys;     // length of the key arrays
+  uint32_t wait_limit;  // polls before a bounded device-side wait gives up
+  int test_stall;       // failure-path test: one tile is never requested
 };
 
 // Parity of the lists the current level consumes: given by the host when it drives

@@ -105,33 +105,23 @@ struct Variant {
   void (*launch)(const Params&, int grid, cudaStream_t);
 };
 
-template <class KT, bool PAIRS, int T, int K, int MINB>
-void launch_partition(const Params& P, int grid, cudaStream_t st) {
-  k_partition<KT, PAIRS, T, K, MINB><<<grid, T, 0, st>>>(P);
-}
-
-template <class KT, bool PAIRS, int T, int K, int MINB>
-Variant make_variant() {
-  return Variant{T, K, (const void*)k_partition<KT, PAIRS, T, K, MINB>, 0,
-                 &launch_partition<KT, PAIRS, T, K, MINB>};
-}
-
-template <class KT, bool PAIRS, int T, int K, int STAGES>
+template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
 void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
-  k_partition_tma<KT, PAIRS, T, K, STAGES>
-      <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES>::smem, st>>>(P);
+  k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>
+      <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, st>>>(P);
 }
 
-template <class KT, bool PAIRS, int T, int K, int STAGES>
+template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK = 256, int MINB = 1>
 Variant make_tma_variant() {
-  const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES>;
-  const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES>::smem;
+  const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>;
+  const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES>};
+  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>};
 }
 
-// Tile shapes offered to the autotuner: keys per tile = threads * keys-per-thread.
-// 0-2: TMA-fed persistent kernels; 3: the register-loading kernel.
+// Tile shapes offered to the autotuner (BQS_OPT_TILE 0..4), all TMA-fed persistent
+// kernels: keys per tile = threads * keys-per-thread, STAGES tiles in flight per block;
+// 3 and 4 have smaller shared-memory footprints so that 3-4 blocks share an SM.
 template <class KT, bool PAIRS>
 const std::vector<Variant>& variants() {
   static const std::vector<Variant> v = [] {
@@ -140,12 +130,16 @@ const std::vector<Variant>& variants() {
       r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 3>());
       r.push_back(make_tma_variant<KT, PAIRS, 256, 32, 2>());
       r.push_back(make_tma_variant<KT, PAIRS, 512, 16, 2>());
-      r.push_back(make_variant<KT, PAIRS, 256, 16, 4>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 2, 128>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 4, 128>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 2, 64, 4>());
     } else {
       r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 3>());
       r.push_back(make_tma_variant<KT, PAIRS, 256, 16, 2>());
       r.push_back(make_tma_variant<KT, PAIRS, 512, 8, 2>());
-      r.push_back(make_variant<KT, PAIRS, 256, 8, 4>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 2, 128>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 4, 4, 128>());
+      r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 2, 64, 4>());
     }
     return r;
   }();
@@ -332,6 +326,8 @@ int run_call(const Call& c, Stats& st) {
   P.route_children = c.partition_only ? 0 : 1;
   P.tile = tile;
   P.n_keys = c.n;
+  P.wait_limit = (uint32_t)c.opt.wait_limit;
+  P.test_stall = 0;
   {
     int64_t top = c.n;  // depth limit 2*floor(log2 n)+3 of the largest array (Sec. 2)
     int lg = 0;
@@ -430,7 +426,9 @@ int run_call(const Call& c, Stats& st) {
         ++ev_used;
         BQS_CK(cudaEventRecord(e0, s));
       }
+      P.test_stall = (level == 0 && c.opt.test_stall) ? 1 : 0;
       var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s);
+      P.test_stall = 0;
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);

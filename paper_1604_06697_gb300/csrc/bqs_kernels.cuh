@@ -2,8 +2,7 @@
 //
 //   k_init_*      first work lists from the caller's array / segments
 //   k_pivot       pivots that need a whole block (sqrt(n) sample, depth fallback)
-//   k_partition   Algorithm 3 per tile: compare, buffer outcomes, rearrange
-//                 (register-loading form; the TMA-fed form is in bqs_tma.cuh)
+//   (the partition step itself, Algorithm 3 per tile, is k_partition_tma in bqs_tma.cuh)
 //   k_bookkeep    children of every partitioned segment (Quicksort main loop)
 //   k_fill        writes the class equal to a pivot into the final buffer
 // The small-segment sorting network is in bqs_small.cuh.
@@ -357,174 +356,6 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
       segs[s].pval = piv.v;
     }
     __syncthreads();
-  }
-}
-
-// ---- the block partition step -----------------------------------------------------------
-
-// Algorithm 3, one tile per iteration.  A tile is THREADS*KPT consecutive keys of the
-// global index space (aligned to its size), clipped to one segment.
-//  scan phase:   every thread loads KPT keys with 16-byte loads and compares them with
-//                the pivot; the outcomes stay in registers (the offset buffers of Sec. 3).
-//  offsets:      per key round, a warp ballot gives the warp's "<" and ">" masks; their
-//                population counts give each key's rank in its warp and the warp's total;
-//                a scan over the warp totals gives tile offsets.
-//  reservation:  one 64-bit atomic on the segment's cursor reserves the tile's run of
-//                "<" keys (growing from the segment's start) and of ">" keys (growing
-//                from its end) at once.
-//  rearrange:    keys are staged in shared memory in output order and written out with
-//                consecutive threads on consecutive addresses.  Keys equal to the pivot
-//                are only counted; k_fill writes them.
-template <class KT, bool PAIRS, int THREADS, int KPT, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_partition(Params P) {
-  using U = typename KT::U;
-  constexpr int VEC = 16 / sizeof(U);
-  constexpr int NV = KPT / VEC;
-  constexpr int TILE = THREADS * KPT;
-  constexpr int WARPS = THREADS / 32;
-  static_assert(KPT % VEC == 0 && KPT <= 32 && TILE <= 32768, "tile shape");
-
-  __shared__ __align__(16) U s_key[TILE];
-  __shared__ __align__(16) uint32_t s_val[PAIRS ? TILE : 1];
-  __shared__ uint32_t s_wcnt[WARPS];            // (#<) | (#>) << 16 per warp
-  __shared__ unsigned long long s_base;
-  __shared__ uint32_t s_tseg[THREADS];
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int pp = level_parity(P, P.p);
-  const unsigned long long lc = P.ctrl->lists[pp].large;
-  const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
-  const Seg* __restrict__ segs = P.l.large[pp];
-  unsigned long long* cursor = P.l.cursor[pp];
-
-  for (uint32_t round = 0;; ++round) {
-    // Segment of each of this block's next THREADS tiles, one binary search per thread.
-    const uint64_t first = (uint64_t)blockIdx.x + (uint64_t)round * THREADS * gridDim.x;
-    if (first >= ntiles) break;
-    {
-      const uint64_t t = first + (uint64_t)threadIdx.x * gridDim.x;
-      if (t < ntiles) {
-        uint32_t lo = 0, hi = nseg;            // last segment with tile0 <= t
-        while (hi - lo > 1) {
-          uint32_t mid = (lo + hi) >> 1;
-          if (segs[mid].tile0 <= t) lo = mid; else hi = mid;
-        }
-        s_tseg[threadIdx.x] = lo;
-      }
-    }
-    __syncthreads();
-    for (int it = 0; it < THREADS; ++it) {
-      const uint64_t t = first + (uint64_t)it * gridDim.x;
-      if (t >= ntiles) break;
-      const uint32_t si = s_tseg[it];
-      const Seg sg = segs[si];
-      const U* __restrict__ src = (const U*)P.b.key[sg.parity];
-      U* __restrict__ dst = (U*)P.b.key[sg.parity ^ 1];
-      const uint32_t* __restrict__ vsrc = P.b.val[sg.parity];
-      uint32_t* __restrict__ vdst = P.b.val[sg.parity ^ 1];
-      const int64_t abase = tile_origin(sg.off) + (int64_t)(t - sg.tile0) * TILE;
-      const int64_t lo = max(abase, sg.off), hi = min(abase + TILE, sg.off + sg.len);
-      const U pk = KT::ord((U)sg.pkey);
-      const uint32_t pv = sg.pval;
-
-      // Scan phase: load and compare.
-      U key[KPT];
-      uint32_t val[PAIRS ? KPT : 1];
-#pragma unroll
-      for (int j = 0; j < NV; ++j) {
-        const int64_t i0 = abase + (int64_t)(j * THREADS + threadIdx.x) * VEC;
-        if (i0 >= lo && i0 + VEC <= hi) {
-          union { uint4 v; U e[VEC]; } u;
-          u.v = __ldcs(reinterpret_cast<const uint4*>(src + i0));
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) key[j * VEC + e] = u.e[e];
-          if constexpr (PAIRS) {
-            if constexpr (VEC == 4) {
-              uint4 w = __ldcs(reinterpret_cast<const uint4*>(vsrc + i0));
-              val[j * 4 + 0] = w.x; val[j * 4 + 1] = w.y; val[j * 4 + 2] = w.z; val[j * 4 + 3] = w.w;
-            } else {
-              uint2 w = __ldcs(reinterpret_cast<const uint2*>(vsrc + i0));
-              val[j * 2 + 0] = w.x; val[j * 2 + 1] = w.y;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const int64_t i = i0 + e;
-            key[j * VEC + e] = (i >= lo && i < hi) ? src[i] : U(0);
-            if constexpr (PAIRS) val[j * VEC + e] = (i >= lo && i < hi) ? vsrc[i] : 0u;
-          }
-        }
-      }
-      uint32_t lt_bits = 0, gt_bits = 0;   // the thread's outcome buffer
-#pragma unroll
-      for (int j = 0; j < NV; ++j) {
-        const int64_t i0 = abase + (int64_t)(j * THREADS + threadIdx.x) * VEC;
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const int r = j * VEC + e;
-          const bool valid = (i0 + e >= lo) && (i0 + e < hi);
-          const U k = KT::ord(key[r]);
-          const uint32_t v = PAIRS ? val[r] : 0u;
-          lt_bits |= (uint32_t)(valid && elem_less<PAIRS>(k, v, pk, pv)) << r;
-          gt_bits |= (uint32_t)(valid && elem_less<PAIRS>(pk, pv, k, v)) << r;
-        }
-      }
-
-      // Offsets: warp totals from ballots, then a scan over the warps.
-      uint32_t wlt = 0, wgt = 0;
-#pragma unroll
-      for (int r = 0; r < KPT; ++r) {
-        wlt += __popc(__ballot_sync(~0u, (lt_bits >> r) & 1));
-        wgt += __popc(__ballot_sync(~0u, (gt_bits >> r) & 1));
-      }
-      if (lane == 0) s_wcnt[warp] = wlt | (wgt << 16);
-      __syncthreads();
-      uint32_t off_lt = 0, off_gt = 0, nlt = 0, ngt = 0;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) {
-        const uint32_t c = s_wcnt[w];
-        if (w < warp) { off_lt += c & 0xFFFF; off_gt += c >> 16; }
-        nlt += c & 0xFFFF;
-        ngt += c >> 16;
-      }
-      if (threadIdx.x == 0)   // reservation: one atomic per tile
-        s_base = atomicAdd(&cursor[si], (unsigned long long)nlt | ((unsigned long long)ngt << 32));
-
-      // Stage in output order: "<" keys at [0, nlt), ">" keys at [nlt, nlt+ngt).
-      const unsigned below = lanemask_lt();
-      uint32_t run_lt = off_lt, run_gt = nlt + off_gt;
-#pragma unroll
-      for (int r = 0; r < KPT; ++r) {
-        const unsigned mlt = __ballot_sync(~0u, (lt_bits >> r) & 1);
-        const unsigned mgt = __ballot_sync(~0u, (gt_bits >> r) & 1);
-        if ((lt_bits >> r) & 1) {
-          const uint32_t pos = run_lt + __popc(mlt & below);
-          s_key[pos] = key[r];
-          if constexpr (PAIRS) s_val[pos] = val[r];
-        }
-        if ((gt_bits >> r) & 1) {
-          const uint32_t pos = run_gt + __popc(mgt & below);
-          s_key[pos] = key[r];
-          if constexpr (PAIRS) s_val[pos] = val[r];
-        }
-        run_lt += __popc(mlt);
-        run_gt += __popc(mgt);
-      }
-      __syncthreads();
-
-      // Rearrangement: coalesced write-out of the two runs.
-      const unsigned long long base = s_base;
-      const int64_t left = sg.off + (int64_t)(uint32_t)base;
-      const int64_t right = sg.off + sg.len - (int64_t)(uint32_t)(base >> 32) - ngt;
-      const uint32_t nout = nlt + ngt;
-      for (uint32_t i = threadIdx.x; i < nout; i += THREADS) {
-        const int64_t g = i < nlt ? left + i : right + (i - nlt);
-        dst[g] = s_key[i];
-        if constexpr (PAIRS) vdst[g] = s_val[i];
-      }
-      __syncthreads();
-    }
   }
 }
 

@@ -51,10 +51,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
       ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^26 polls (seconds), records
-// a timeout in the device status word and reports failure to the caller.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Ctrl* ctrl) {
-  for (uint32_t it = 0; it < (1u << 26); ++it) {
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (2^26 by default,
+// seconds), records a timeout in the device status word and reports failure to the
+// caller, which then leaves the kernel instead of hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Ctrl* ctrl,
+                                                  uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(32);
   }
@@ -94,11 +96,11 @@ struct TileInfo {
   int32_t pad;
 };
 
-template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES>
+template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES, int CHUNK_ = 256>
 struct TmaShape {
   using U = typename KT::U;
   static constexpr int TILE = THREADS * KPT;
-  static constexpr int CHUNK = 256;       // tiles whose descriptors are looked up at once
+  static constexpr int CHUNK = CHUNK_;    // tiles whose descriptors are looked up at once
   static constexpr size_t in_bytes = (size_t)STAGES * TILE * sizeof(U);
   static constexpr size_t vin_bytes = PAIRS ? (size_t)STAGES * TILE * 4 : 0;
   static constexpr size_t out_bytes = (size_t)TILE * sizeof(U);
@@ -107,10 +109,10 @@ struct TmaShape {
   static constexpr size_t smem = in_bytes + vin_bytes + out_bytes + vout_bytes + info_bytes;
 };
 
-template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES>
-__global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
+template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES, int CHUNK_ = 256, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   using U = typename KT::U;
-  using S = TmaShape<KT, PAIRS, THREADS, KPT, STAGES>;
+  using S = TmaShape<KT, PAIRS, THREADS, KPT, STAGES, CHUNK_>;
   using CT = typename Cmp<KT>::T;
   constexpr int TILE = S::TILE;
   constexpr int VEC = 16 / sizeof(U);
@@ -171,6 +173,9 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
   // 16-byte group is read with plain loads by the issuing thread.
   auto issue = [&](uint32_t i) {
     const int st = i % STAGES;
+    // Failure-path test (BQS_OPT_TEST_STALL): the first tile of block 0 is never
+    // requested, so its mbarrier phase never completes and the bounded waits run out.
+    if (P.test_stall && blockIdx.x == 0 && i == 0) return;
     const TileInfo& ti = s_info[((i / CHUNK) & 1) * CHUNK + (i % CHUNK)];
     const int64_t abase = tile_origin(ti.off) + (int64_t)(ti.parity >> 1) * TILE;
     const int64_t lo = max(abase, ti.off), hi = min(abase + TILE, ti.off + ti.len);
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
       // (needed once the refills run STAGES tiles ahead into it).
       lookup_chunk(i / CHUNK + 1);
     }
-    if (!mbar_wait_bounded(&s_bar[st], parity, P.ctrl)) s_abort = 1;
+    if (!mbar_wait_bounded(&s_bar[st], parity, P.ctrl, P.wait_limit)) s_abort = 1;
     __syncthreads();
     if (s_abort) break;
 
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(THREADS) k_partition_tma(Params P) {
     // Let the copies already issued (tiles i .. i+STAGES-1) land before the block's
     // shared memory goes away; each of these waits is bounded too.
     for (uint32_t j = i; j < count && j < i + STAGES; ++j)
-      (void)mbar_wait_bounded(&s_bar[j % STAGES], (j / STAGES) & 1, P.ctrl);
+      (void)mbar_wait_bounded(&s_bar[j % STAGES], (j / STAGES) & 1, P.ctrl, P.wait_limit);
   }
 }
 

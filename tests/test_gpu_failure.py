@@ -1,0 +1,47 @@
+"""Failure detection without a GPU fault.
+
+The partition kernel's waits on its shared-memory pipeline are bounded.  A test-only
+option leaves one tile unrequested, so that wait runs out: the kernel records a
+timeout in the device status word, waits (again bounded) for the copies it did
+issue, and returns.  The call reports BQS_ERR_TIMEOUT and the device stays usable:
+the next sort is correct.  Host-side failures (bad arguments, decreasing offsets)
+are covered in test_gpu_sort.py and test_abi.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06697_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bqs():
+    import torch
+    from paper_1604_06697_gb300 import build
+    build.build()
+    import paper_1604_06697_gb300 as m
+    torch.cuda.init()
+    return m
+
+
+def test_bounded_wait_times_out_and_device_stays_usable(bqs):
+    import torch
+    a = inputs.make_keys(1 << 24, "int32", "uniform", seed=8)   # every block owns tiles
+    t = torch.from_numpy(a).cuda()
+    old_limit = bqs.get_option("wait_limit")
+    bqs.set_option("wait_limit", 1 << 16)      # give up after ~10 ms instead of seconds
+    bqs.set_option("test_stall", 1)
+    try:
+        with pytest.raises(bqs.BqsError) as e:
+            bqs.sort(t)
+        assert e.value.status == -4                  # BQS_ERR_TIMEOUT
+    finally:
+        bqs.set_option("test_stall", 0)
+        bqs.set_option("wait_limit", old_limit)
+    torch.cuda.synchronize()                         # no sticky CUDA error
+    t2 = torch.from_numpy(a).cuda()
+    bqs.sort(t2)
+    torch.cuda.synchronize()
+    assert np.array_equal(t2.cpu().numpy(), oracle.sort(a))

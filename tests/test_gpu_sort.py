@@ -63,7 +63,7 @@ def test_sort_matches_oracle_edge_sizes(bqs, dtype, dist):
 
 
 @pytest.mark.parametrize("pivot", [0, 1])
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_sort_pivot_rules_and_tiles(bqs, dtype, tile, pivot):
     bqs.set_option("pivot", pivot)
