@@ -138,6 +138,36 @@ def time_oracle(a, seconds: float):
                       f"single thread, {dt:.1f} s"}
 
 
+def time_library_sorts(a, host_keys, seconds: float):
+    """std::sort on one host thread and a parallel sort on every host core, each on
+    the full workload (or a 2^24-key prefix if one std::sort would take too long)."""
+    import numpy as np
+
+    from oracle import cpu_baselines
+
+    cpu_baselines.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = []
+    for threads in (1, cores):
+        m = host_keys.size if threads > 1 or host_keys.size <= (1 << 26) else 1 << 24
+        keys, reps, t_sort = 0, 0, 0.0
+        work = np.empty(m, host_keys.dtype)
+        kind = ""
+        while True:
+            work[:] = host_keys[:m]
+            t0 = time.perf_counter()
+            kind = cpu_baselines.sort_inplace(work, threads)
+            t_sort += time.perf_counter() - t0
+            keys += m
+            reps += 1
+            if t_sort >= seconds / 2 or reps >= 3:
+                break
+        out.append({"value": keys / t_sort, "unit": "keys/s", "cores": threads, "kind": kind,
+                    "sample": f"{reps} x {kind} of the first 2^{int(math.log2(m))} keys of the "
+                              f"workload, {threads} thread(s), {t_sort:.1f} s"})
+    return out
+
+
 # ---- clocks ----------------------------------------------------------------------------------
 
 class ClockSampler:
@@ -348,6 +378,7 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = time_oracle(a, a.cpu_seconds)
+        cpu["library_sorts"] = time_library_sorts(a, host, a.cpu_seconds)
 
     peak, peak_kind = measured_peak_gbs()
     achieved = (part_bytes / (part_ms / 1e3)) / 1e9 if part_ms > 0 else None

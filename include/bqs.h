@@ -166,10 +166,17 @@ typedef enum {
                                (-1 = as large as one block holds; 0 = off, the default) */
   BQS_OPT_WAIT_LIMIT = 6,   /* polls before a bounded device-side wait gives up and the
                                call returns BQS_ERR_TIMEOUT (default 2^26, seconds) */
-  BQS_OPT_TEST_STALL = 7    /* failure-path testing: 1 makes the first partition launch
+  BQS_OPT_TEST_STALL = 7,   /* failure-path testing: 1 makes the first partition launch
                                of a sort leave one tile unrequested, so its bounded wait
                                runs out (the call returns BQS_ERR_TIMEOUT, the device
                                stays usable; the keys are then unspecified) */
+  BQS_OPT_LEVEL_LOOP = 8    /* 0 (default): after every level the host reads the next
+                               level's work counts and sizes its launches to them;
+                               1: every kernel reads its counts on the device and the
+                               host keeps up to 4 levels enqueued ahead, checking a
+                               pinned per-level flag a few levels behind (sorts and
+                               segmented sorts; bqs_partition and bqs_sort_noalloc
+                               always use 0) */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

@@ -107,6 +107,12 @@ struct Ctrl {
   unsigned long long local_segs;
   unsigned long long local_keys;
   unsigned long long fallbacks;
+  // device-driven level loop (host enqueues levels ahead)
+  int more[8];                      // per level (mod 8): another level has work
+  unsigned long long levels_run;    // levels that partitioned something
+  unsigned long long active_total;  // sum of partitioned keys over those levels
+  unsigned long long local_runs;    // segments finished by the single-block sort
+  unsigned long long small_runs;    // segments finished by the sorting networks
 };
 
 struct Bufs {

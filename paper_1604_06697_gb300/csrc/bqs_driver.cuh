@@ -225,6 +225,48 @@ inline cudaStream_t helper_stream() {
   return hs;
 }
 
+// One level of the device-driven loop: every kernel takes the level parity and its work
+// counts from the control block, so the grids are fixed (persistent) sizes.  Optional
+// events bracket the partition launch for BQS_OPT_TIMING.
+template <class KT, bool PAIRS>
+void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, bool local_on,
+                        cudaEvent_t e0, cudaEvent_t e1) {
+  const int sms = sm_count();
+  k_level_begin<<<1, 32, 0, s>>>(P);
+  k_pivot<KT, PAIRS><<<8 * sms, 256, 0, s>>>(P);
+  if (e0) cudaEventRecord(e0, s);
+  var.launch(P, persistent_grid(var.fn, var.threads, var.smem), s);
+  if (e1) cudaEventRecord(e1, s);
+  k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P);
+  k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
+  if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), s);
+  k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
+  k_small_block<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
+}
+
+// Pinned flags and events of the calling thread for the device-driven host loop.
+struct LevelRing {
+  int* flags = nullptr;            // pinned, 8 entries
+  cudaEvent_t ev[8] = {};
+  bool ok = false;
+};
+
+inline LevelRing& level_ring() {
+  static thread_local LevelRing r;
+  if (!r.ok) {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, 8 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return r; }
+    r.flags = (int*)p;
+    for (auto& e : r.ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return r;
+      }
+    r.ok = true;
+  }
+  return r;
+}
+
 // Adds to the graph being captured on `s` a conditional while node whose body is one
 // level of the sort, recorded on a helper stream with fixed (persistent) grids; the
 // kernels read the level parity and the work counts from the control block, and
@@ -254,21 +296,81 @@ int capture_level_loop(const Params& P, const Variant& var, cudaStream_t s, int 
   cudaStream_t hs = helper_stream();
   if (!hs) return kErrCuda;
   BQS_CK(cudaStreamBeginCaptureToGraph(hs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  const int sms = sm_count();
-  k_level_begin<<<1, 32, 0, hs>>>(P);
-  k_pivot<KT, PAIRS><<<8 * sms, 256, 0, hs>>>(P);
-  var.launch(P, persistent_grid(var.fn, var.threads, var.smem), hs);
-  k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, hs>>>(P);
-  k_fill<KT, PAIRS><<<4 * sms, 256, 0, hs>>>(P, 0);
-  if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), hs);
-  k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, hs>>>(P, 0);
-  k_small_block<KT, PAIRS><<<16 * sms, 256, 0, hs>>>(P, 0);
+  enqueue_level_body<KT, PAIRS>(P, var, hs, local_on, nullptr, nullptr);
   k_level_end<<<1, 32, 0, hs>>>(P, h, max_levels);
   const cudaError_t launch_err = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   const cudaError_t end_err = cudaStreamEndCapture(hs, &captured);
   if (launch_err != cudaSuccess) return fail_cuda(launch_err, "recording the level loop");
   if (end_err != cudaSuccess) return fail_cuda(end_err, "cudaStreamEndCapture(level loop body)");
+  return kOk;
+}
+
+// The level loop driven by device-side counts on an ordinary stream: the host keeps up
+// to kAhead levels enqueued and, before adding level j + kAhead, waits for level j's
+// flag (copied to pinned memory behind an event).  Levels enqueued past the last one
+// find empty lists and return at once.  Returns after the last level has run.
+template <class KT, bool PAIRS>
+int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_levels,
+                     bool local_on, bool timing, int test_stall, Ctrl* host, Stats& st) {
+  constexpr int kAhead = 4;   // < 8, the size of the flag ring
+  LevelRing& ring = level_ring();
+  if (!ring.ok) return kErrNoMem;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
+  std::vector<char> partitioned;
+  int enq = 0, checked = 0;
+  for (bool more = true; more;) {
+    for (; enq < checked + kAhead && enq <= max_levels; ++enq) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (timing) {
+        if ((size_t)enq == evs.size()) {
+          cudaEvent_t a, b;
+          BQS_CK(cudaEventCreate(&a));
+          BQS_CK(cudaEventCreate(&b));
+          evs.emplace_back(a, b);
+        }
+        e0 = evs[enq].first; e1 = evs[enq].second;
+      }
+      P.test_stall = enq == 0 ? test_stall : 0;
+      enqueue_level_body<KT, PAIRS>(P, var, s, local_on, e0, e1);
+      k_level_step<<<1, 32, 0, s>>>(P, max_levels);
+      BQS_CK(cudaGetLastError());
+      BQS_CK(cudaMemcpyAsync(&ring.flags[enq & 7], &P.ctrl->more[enq & 7], sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+      BQS_CK(cudaEventRecord(ring.ev[enq & 7], s));
+      st.kernel_launches += local_on ? 9 : 8;
+      st.partition_launches += 1;
+    }
+    if (checked == enq) return kErrInternal;   // the device bounds the levels first
+    BQS_CK(cudaEventSynchronize(ring.ev[checked & 7]));
+    const int f = *(volatile int*)&ring.flags[checked & 7];
+    partitioned.push_back((f & 2) != 0);
+    more = (f & 1) != 0;
+    ++checked;
+  }
+  BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  BQS_CK(cudaStreamSynchronize(s));
+  if (host->status) return status_code(host->status);
+  st.levels = (int64_t)host->levels_run;
+  st.active_keys = (int64_t)host->active_total;
+  st.local_segments = (int64_t)host->local_runs;
+  st.small_segments = (int64_t)host->small_runs;
+  st.moved_keys = (int64_t)host->moved_keys;
+  st.equal_keys = (int64_t)host->equal_keys;
+  st.small_keys = (int64_t)host->small_keys;
+  st.local_keys = (int64_t)host->local_keys;
+  st.fallback_pivots = (int64_t)host->fallbacks;
+  st.partition_bytes_per_key = (double)sizeof(typename KT::U) + (PAIRS ? 4.0 : 0.0);
+  if (timing) {
+    double ms = 0;
+    for (size_t i = 0; i < partitioned.size(); ++i) {
+      if (!partitioned[i]) continue;
+      float t = 0;
+      BQS_CK(cudaEventElapsedTime(&t, evs[i].first, evs[i].second));
+      ms += t;
+    }
+    st.partition_ms = ms;
+  }
   return kOk;
 }
 
@@ -362,6 +464,20 @@ int run_call(const Call& c, Stats& st) {
     P.p = 0;
     st.kernel_launches += 10;   // per level
     return capture_level_loop<KT, PAIRS>(P, var, s, max_levels, local_cutoff > small_cutoff);
+  } else if (!c.fixed_ws && !c.partition_only && c.opt.level_loop == 1) {
+    if (c.seg_offsets) {
+      const int g = (int)std::min<int64_t>((c.nseg + 255) / 256, 4 * sm_count());
+      k_init_segments<KT, PAIRS><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
+    } else {
+      k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
+    }
+    st.kernel_launches += 1;
+    BQS_CK(cudaGetLastError());
+    const int max_levels = P.depth_limit + 8 * (int)sizeof(U) + 40;
+    P.device_loop = 1;
+    P.p = 0;
+    return run_levels_ahead<KT, PAIRS>(P, var, s, max_levels, local_cutoff > small_cutoff, timing,
+                                       c.opt.test_stall ? 1 : 0, host, st);
   } else if (c.partition_only) {
     k_init_partition<KT><<<1, 32, 0, s>>>(P, c.n, c.pivot_raw);
     st.kernel_launches += 1;
@@ -466,6 +582,8 @@ int run_call(const Call& c, Stats& st) {
   }
   st.moved_keys = (int64_t)host->moved_keys;
   st.equal_keys = (int64_t)host->equal_keys;
+  st.small_keys = (int64_t)host->small_keys;
+  st.local_keys = (int64_t)host->local_keys;
   st.fallback_pivots = (int64_t)host->fallbacks;
   st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
   if (timing && ev_used) {

@@ -9,13 +9,19 @@
 
 namespace bqs {
 
-// First node of the body: the lists this level produces start empty.
+__device__ __forceinline__ void clear_counts(ListCounts* l) {
+  l->large = 0; l->fill = 0; l->large_keys = 0;
+  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0;
+}
+
+// First kernel of a level: the lists this level produces start empty.  After an error
+// (levels enqueued ahead of the host's check) the level's own lists are emptied too,
+// so every later kernel of the call finds no work.
 static __global__ void k_level_begin(Params P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int q = (P.ctrl->level & 1) ^ 1;
-    ListCounts* l = &P.ctrl->lists[q];
-    l->large = 0; l->fill = 0; l->large_keys = 0;
-    l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0;
+    const int p = P.ctrl->level & 1;
+    clear_counts(&P.ctrl->lists[p ^ 1]);
+    if (P.ctrl->status != 0) clear_counts(&P.ctrl->lists[p]);
   }
 }
 
@@ -35,6 +41,34 @@ static __global__ void k_level_end(Params P, cudaGraphConditionalHandle h, int m
     }
     c->level += 1;
     cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
+// Last kernel of one level when the host enqueues levels ahead without reading counts:
+// records in a ring indexed by level whether another level has work (bit 0) and
+// whether this level partitioned anything (bit 1), adds the level's statistics and
+// advances the level.
+static __global__ void k_level_step(Params P, int max_levels) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctrl* c = P.ctrl;
+    const int lvl = c->level;
+    const int p = lvl & 1, q = p ^ 1;
+    const ListCounts& cur = c->lists[p];
+    const ListCounts& n = c->lists[q];
+    if ((unsigned)cur.large != 0u) {
+      c->levels_run += 1;
+      c->active_total += cur.large_keys;
+    }
+    c->local_runs += cur.local;
+    c->small_runs += cur.small + cur.tiny;
+    bool more = ((unsigned)n.large | n.small | n.tiny | n.local) != 0u;
+    if (c->status != 0) more = false;
+    if (more && lvl + 1 > max_levels) {
+      c->status = kStatusOverflow;
+      more = false;
+    }
+    c->more[lvl & 7] = (more ? 1 : 0) | ((unsigned)cur.large != 0u ? 2 : 0);
+    c->level = lvl + 1;
   }
 }
 

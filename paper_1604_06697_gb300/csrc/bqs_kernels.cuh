@@ -136,8 +136,12 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
     const int leader = __ffs(m) - 1;
     unsigned int* counter = kind == 0 ? &c->lists[q].tiny : kind == 1 ? &c->lists[q].small : &c->lists[q].local;
     Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : P.l.local[q];
+    const unsigned keys = __reduce_add_sync(~0u, mine ? (unsigned)len : 0u);  // <= 32 * 2^14
     unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    if (lane == leader) {
+      base = atomicAdd(counter, (unsigned)__popc(m));
+      atomicAdd(kind == 2 ? &c->local_keys : &c->small_keys, (unsigned long long)keys);
+    }
     base = __shfl_sync(~0u, base, leader);
     if (mine) {
       const unsigned int slot = base + __popc(m & below);
