@@ -57,6 +57,7 @@ def parse_args(argv=None):
     ap.add_argument("--tile", type=int, default=None)
     ap.add_argument("--small", type=int, default=None)
     ap.add_argument("--local", type=int, default=None)
+    ap.add_argument("--small-sort", type=int, default=None, choices=[0, 1])
     return ap.parse_args(argv)
 
 
@@ -295,7 +296,8 @@ def run_ours(a):
         from paper_1604_06697_gb300 import autotune
         tuned = autotune.tune(a.dtype, n, kind="sort")["config"]
     else:
-        for name, v in (("tile", a.tile), ("small_cutoff", a.small), ("local_cutoff", a.local)):
+        for name, v in (("tile", a.tile), ("small_cutoff", a.small), ("local_cutoff", a.local),
+                        ("small_sort", a.small_sort)):
             if v is not None:
                 bqs.set_option(name, v)
     host = inputs.make_keys(n, a.dtype, a.dist, a.seed)

@@ -170,13 +170,18 @@ typedef enum {
                                of a sort leave one tile unrequested, so its bounded wait
                                runs out (the call returns BQS_ERR_TIMEOUT, the device
                                stays usable; the keys are then unspecified) */
-  BQS_OPT_LEVEL_LOOP = 8    /* 0 (default): after every level the host reads the next
+  BQS_OPT_LEVEL_LOOP = 8,   /* 0 (default): after every level the host reads the next
                                level's work counts and sizes its launches to them;
                                1: every kernel reads its counts on the device and the
                                host keeps up to 4 levels enqueued ahead, checking a
                                pinned per-level flag a few levels behind (sorts and
                                segmented sorts; bqs_partition and bqs_sort_noalloc
                                always use 0) */
+  BQS_OPT_SMALL_SORT = 9    /* sorting network for segments of 257 .. small-cutoff keys:
+                               0 (default) = one warp per segment up to 1024 keys and
+                               one 64-thread (32-bit keys) or 128-thread (64-bit keys)
+                               block above; 1 = one 256-thread block per segment.
+                               Key-value sorts always use 256-thread blocks. */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

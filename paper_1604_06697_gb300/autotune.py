@@ -1,8 +1,9 @@
 """Autotuner for the sort's launch shape.
 
 Chooses, for one workload class (dtype, size bucket, single array or batch), the
-partition tile variant (threads x keys per thread), the small-segment cutoff and
-the single-block local-sort cutoff by timing every candidate on a synthetic input
+partition tile variant (threads x keys per thread), the small-segment cutoff, the
+small-segment network shape (one warp / warp group per segment, or one 256-thread
+block) and the single-block local-sort cutoff by timing every candidate on a synthetic input
 of that class with CUDA events.  Results are cached in a JSON file keyed by GPU
 name, dtype, workload kind and log2 size bucket, so a later process applies the
 choice without re-timing.  The tuner only sets the library's options; every
@@ -20,6 +21,8 @@ from . import inputs
 TILES = (0, 1, 2, 3, 4, 5)     # TMA partition variants (see bqs_set_option(BQS_OPT_TILE))
 SMALL_CUTOFFS = (256, 1024, 2048)
 LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
+SMALL_SORTS = (0, 1)           # warp / warp-group networks, or 256-thread block networks
+KNOBS = ("tile", "small_cutoff", "local_cutoff", "small_sort")
 
 
 def default_cache_path() -> str:
@@ -51,7 +54,7 @@ def _store(path, table):
 
 def apply(config: dict) -> None:
     import paper_1604_06697_gb300 as bqs
-    for k in ("tile", "small_cutoff", "local_cutoff"):
+    for k in KNOBS:
         if k in config:
             bqs.set_option(k, int(config[k]))
 
@@ -110,10 +113,11 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
         def prep():
             work.copy_(src)
 
-    saved = {k: bqs.get_option(k) for k in ("tile", "small_cutoff", "local_cutoff")}
+    saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
-    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l)
-                           for t, s, l in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS)]
+    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w)
+                           for t, s, l, w in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
+                                                               SMALL_SORTS)]
     try:
         for cfg in cands:
             apply(cfg)

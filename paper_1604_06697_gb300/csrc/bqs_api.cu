@@ -241,6 +241,10 @@ int bqs_set_option(int32_t opt, int64_t value) {
       if (value < 0 || value > 1) return BQS_ERR_INVALID;
       g_opt.level_loop = value;
       return BQS_OK;
+    case BQS_OPT_SMALL_SORT:
+      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      g_opt.small_sort = value;
+      return BQS_OK;
     default:
       return BQS_ERR_UNSUPPORTED;
   }
@@ -259,6 +263,7 @@ int bqs_get_option(int32_t opt, int64_t* value) {
     case BQS_OPT_WAIT_LIMIT: *value = g_opt.wait_limit; return BQS_OK;
     case BQS_OPT_TEST_STALL: *value = g_opt.test_stall; return BQS_OK;
     case BQS_OPT_LEVEL_LOOP: *value = g_opt.level_loop; return BQS_OK;
+    case BQS_OPT_SMALL_SORT: *value = g_opt.small_sort; return BQS_OK;
     default: return BQS_ERR_UNSUPPORTED;
   }
 }

@@ -94,6 +94,7 @@ struct ListCounts {
   unsigned int tiny;    // small segments of at most kWarpSortMax keys
   unsigned int todo;    // large segments whose pivot k_pivot chooses
   unsigned int local;
+  unsigned int group;   // small segments above the one-warp size (key-only sorts)
 };
 
 struct Ctrl {
@@ -127,6 +128,7 @@ struct Lists {
   unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
   Run* small[2];
   Run* tiny[2];
+  Run* group[2];
   uint32_t* todo[2];              // slots of large segments waiting for k_pivot
   Run* local[2];
   Fill* fill[2];
@@ -148,6 +150,8 @@ struct Params {
   int64_t n_keys;     // length of the key arrays
   uint32_t wait_limit;  // polls before a bounded device-side wait gives up
   int test_stall;       // failure-path test: one tile is never requested
+  int small_sort;       // 0: warp / warp-group networks for key-only sorts; 1: 256-thread blocks
+  int group_min;        // small segments longer than this go to the `group` list
 };
 
 // Parity of the lists the current level consumes: given by the host when it drives

@@ -25,7 +25,7 @@ namespace bqs {
 
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
-  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0};
+  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -54,6 +54,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.large[i] = take((size_t)L.cap_large * sizeof(Seg));
     L.cursor[i] = take((size_t)L.cap_large * 8);
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.group[i] = take((size_t)L.cap_run * sizeof(Run));
     L.tiny[i] = take((size_t)L.cap_run * sizeof(Run));
     L.todo[i] = take((size_t)L.cap_large * sizeof(uint32_t));
     L.local[i] = take((size_t)L.cap_run * sizeof(Run));
@@ -225,6 +226,40 @@ inline cudaStream_t helper_stream() {
   return hs;
 }
 
+// Launches the sorting networks of the `small` list (kWarpSortMax+1 .. group_min keys)
+// and of the `group` list (longer segments, key-only sorts with small_sort = 0).
+// Key-only sorts: one warp per `small` segment (k_small_warps) and one SmallGroup
+// block per `group` segment (k_small_group); key-value sorts, or small_sort = 1: one
+// 256-thread block per `small` segment (k_small_block), and `group` stays empty.
+// Counts are the list lengths when the host knows them (a launch is then skipped when
+// its list is empty); device_counts = true launches persistent grids that read them on
+// the device.  Returns the number of launches.
+template <class KT, bool PAIRS>
+int launch_small(const Params& P, int p, uint32_t small, uint32_t group, bool device_counts,
+                 cudaStream_t s) {
+  const int sms = sm_count();
+  int n = 0;
+  const bool warps = !PAIRS && P.small_sort == 0;
+  if (device_counts || small) {
+    if (warps) {
+      const uint32_t g = device_counts ? 8 * sms : std::min<uint32_t>((small + 3) / 4, 8 * sms);
+      if constexpr (!PAIRS) k_small_warps<KT, PAIRS><<<(int)g, 128, 0, s>>>(P, p);
+    } else {
+      const uint32_t g = device_counts ? 16 * sms : std::min<uint32_t>(small, 16 * sms);
+      k_small_block<KT, PAIRS><<<(int)g, 256, 0, s>>>(P, p);
+    }
+    ++n;
+  }
+  if constexpr (!PAIRS) {
+    if (warps && P.small_cutoff > P.group_min && (device_counts || group)) {
+      const uint32_t g = device_counts ? 16 * sms : std::min<uint32_t>(group, 16 * sms);
+      k_small_group<KT, PAIRS><<<(int)g, SmallGroup<KT>::T, 0, s>>>(P, p);
+      ++n;
+    }
+  }
+  return n;
+}
+
 // One level of the device-driven loop: every kernel takes the level parity and its work
 // counts from the control block, so the grids are fixed (persistent) sizes.  Optional
 // events bracket the partition launch for BQS_OPT_TIMING.
@@ -241,7 +276,7 @@ void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, boo
   k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
   if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), s);
   k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
-  k_small_block<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
+  launch_small<KT, PAIRS>(P, 0, 0, 0, true, s);
 }
 
 // Pinned flags and events of the calling thread for the device-driven host loop.
@@ -338,7 +373,8 @@ int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_level
       BQS_CK(cudaMemcpyAsync(&ring.flags[enq & 7], &P.ctrl->more[enq & 7], sizeof(int),
                              cudaMemcpyDeviceToHost, s));
       BQS_CK(cudaEventRecord(ring.ev[enq & 7], s));
-      st.kernel_launches += local_on ? 9 : 8;
+      st.kernel_launches += (local_on ? 8 : 7) +
+                            ((!PAIRS && P.small_sort == 0 && P.small_cutoff > P.group_min) ? 2 : 1);
       st.partition_launches += 1;
     }
     if (checked == enq) return kErrInternal;   // the device bounds the levels first
@@ -416,6 +452,7 @@ int run_call(const Call& c, Stats& st) {
     P.l.large[i] = (Seg*)(w + L.large[i]);
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
+    P.l.group[i] = (Run*)(w + L.group[i]);
     P.l.tiny[i] = (Run*)(w + L.tiny[i]);
     P.l.todo[i] = (uint32_t*)(w + L.todo[i]);
     P.l.local[i] = (Run*)(w + L.local[i]);
@@ -430,6 +467,10 @@ int run_call(const Call& c, Stats& st) {
   P.n_keys = c.n;
   P.wait_limit = (uint32_t)c.opt.wait_limit;
   P.test_stall = 0;
+  P.small_sort = (int)c.opt.small_sort;
+  // Small segments above one warp's capacity go to the `group` list (key-only sorts with
+  // the warp networks); otherwise every small segment above kWarpSortMax is `small`.
+  P.group_min = (!PAIRS && P.small_sort == 0) ? small_warp_max<KT, PAIRS>() : kMaxSmall;
   {
     int64_t top = c.n;  // depth limit 2*floor(log2 n)+3 of the largest array (Sec. 2)
     int lg = 0;
@@ -496,6 +537,7 @@ int run_call(const Call& c, Stats& st) {
     k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
     st.kernel_launches += 1;
     if (c.n <= small_cutoff && c.n <= kWarpSortMax) cur.tiny = 1;
+    else if (c.n <= small_cutoff && c.n > P.group_min) cur.group = 1;
     else if (c.n <= small_cutoff) cur.small = 1;
     else if (c.n <= local_cutoff) cur.local = 1;
     else {
@@ -560,10 +602,9 @@ int run_call(const Call& c, Stats& st) {
       k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
-    if (cur.small) {
-      st.small_segments += cur.small;
-      k_small_block<KT, PAIRS><<<(int)std::min<uint32_t>(cur.small, 16 * sms), 256, 0, s>>>(P, P.p);
-      st.kernel_launches += 1;
+    if (cur.small || cur.group) {
+      st.small_segments += cur.small + cur.group;
+      st.kernel_launches += launch_small<KT, PAIRS>(P, P.p, cur.small, cur.group, false, s);
     }
     BQS_CK(cudaGetLastError());
     if (!nlarge) break;

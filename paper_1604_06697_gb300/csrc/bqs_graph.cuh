@@ -11,7 +11,7 @@ namespace bqs {
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {
   l->large = 0; l->fill = 0; l->large_keys = 0;
-  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0;
+  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0; l->group = 0;
 }
 
 // First kernel of a level: the lists this level produces start empty.  After an error
@@ -33,7 +33,7 @@ static __global__ void k_level_end(Params P, cudaGraphConditionalHandle h, int m
     Ctrl* c = P.ctrl;
     const int q = (c->level & 1) ^ 1;
     const ListCounts& n = c->lists[q];
-    bool more = ((unsigned)n.large | n.small | n.tiny | n.local) != 0u;
+    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group) != 0u;
     if (c->status != 0) more = false;
     if (more && c->level + 1 > max_levels) {
       c->status = kStatusOverflow;
@@ -60,8 +60,8 @@ static __global__ void k_level_step(Params P, int max_levels) {
       c->active_total += cur.large_keys;
     }
     c->local_runs += cur.local;
-    c->small_runs += cur.small + cur.tiny;
-    bool more = ((unsigned)n.large | n.small | n.tiny | n.local) != 0u;
+    c->small_runs += cur.small + cur.tiny + cur.group;
+    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group) != 0u;
     if (c->status != 0) more = false;
     if (more && lvl + 1 > max_levels) {
       c->status = kStatusOverflow;

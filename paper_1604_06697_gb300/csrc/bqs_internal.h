@@ -30,6 +30,7 @@ struct Options {
   int64_t wait_limit = int64_t(1) << 26;   // polls of a bounded device-side wait
   int64_t test_stall = 0;      // 1: the next sort's first partition launch stalls one tile
   int64_t level_loop = 0;      // 1: the host enqueues levels ahead instead of reading counts
+  int64_t small_sort = 0;      // 1: 256-thread block networks for every small segment
 };
 
 struct Call {

@@ -124,18 +124,20 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
   const bool has = active && len > 0;
   const bool sorted_now = has && len <= P.small_cutoff;
   const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
-  const bool small = sorted_now && !tiny;                // one block per segment
+  const bool group = sorted_now && len > P.group_min;    // one warp group per segment
+  const bool small = sorted_now && !tiny && !group;      // one warp or block per segment
   const bool local = has && !sorted_now && len <= P.local_cutoff;
   const bool large = has && !sorted_now && !local;
 
 #pragma unroll
-  for (int kind = 0; kind < 3; ++kind) {
-    const bool mine = kind == 0 ? tiny : kind == 1 ? small : local;
+  for (int kind = 0; kind < 4; ++kind) {
+    const bool mine = kind == 0 ? tiny : kind == 1 ? small : kind == 2 ? local : group;
     const unsigned m = __ballot_sync(~0u, mine);
     if (!m) continue;
     const int leader = __ffs(m) - 1;
-    unsigned int* counter = kind == 0 ? &c->lists[q].tiny : kind == 1 ? &c->lists[q].small : &c->lists[q].local;
-    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : P.l.local[q];
+    ListCounts& lc = c->lists[q];
+    unsigned int* counter = kind == 0 ? &lc.tiny : kind == 1 ? &lc.small : kind == 2 ? &lc.local : &lc.group;
+    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : kind == 2 ? P.l.local[q] : P.l.group[q];
     const unsigned keys = __reduce_add_sync(~0u, mine ? (unsigned)len : 0u);  // <= 32 * 2^14
     unsigned int base = 0;
     if (lane == leader) {

@@ -75,6 +75,63 @@ __device__ __forceinline__ void load_row(const U* src, U (&x)[R]) {
   }
 }
 
+constexpr int ilog2_c(int v) { return v <= 1 ? 0 : 1 + ilog2_c(v >> 1); }
+
+// Staging layout for rows of R entries (row t = the entries thread t holds).  Entry e
+// of row e / R lives at pos(e): its 16-byte chunk index within the row is XORed with
+// key(row).  Then 16-byte row accesses by 8 consecutive threads (one shared-memory
+// wavefront) touch 8 different bank groups, and striped accesses (entry i*T + t by
+// thread t: coalesced with global memory) by a warp, or a half warp for 8-byte keys,
+// XOR their chunk index with one constant, which keeps their banks distinct.  Rows
+// shorter than one chunk are left unswizzled.
+template <class U, int R>
+struct RowSwizzle {
+  static constexpr int EPC = 16 / (int)sizeof(U);        // entries per 16-byte chunk
+  static constexpr bool kChunked = R >= EPC;
+  static constexpr int C = kChunked ? R / EPC : 1;        // chunks per row
+  static constexpr int LOGC = ilog2_c(C);
+  __device__ static __forceinline__ int key(int row) {
+    if constexpr (!kChunked) return 0;
+    else if constexpr (LOGC >= 3) return row & 7;
+    else return (row >> (3 - LOGC)) & (C - 1);
+  }
+  __device__ static __forceinline__ int pos(int e) { return e ^ (key(e / R) * EPC); }
+};
+
+template <int R, class U>
+__device__ __forceinline__ void swz_store_row(U* base, int row, const U (&x)[R]) {
+  using S = RowSwizzle<U, R>;
+  if constexpr (S::kChunked) {
+    const int kq = S::key(row);
+#pragma unroll
+    for (int c = 0; c < S::C; ++c) {
+      union { uint4 v; U e[S::EPC]; } u;
+#pragma unroll
+      for (int w = 0; w < S::EPC; ++w) u.e[w] = x[c * S::EPC + w];
+      reinterpret_cast<uint4*>(base)[row * S::C + (c ^ kq)] = u.v;
+    }
+  } else {
+    store_row<R>(base + row * R, x);
+  }
+}
+
+template <int R, class U>
+__device__ __forceinline__ void swz_load_row(const U* base, int row, U (&x)[R]) {
+  using S = RowSwizzle<U, R>;
+  if constexpr (S::kChunked) {
+    const int kq = S::key(row);
+#pragma unroll
+    for (int c = 0; c < S::C; ++c) {
+      union { uint4 v; U e[S::EPC]; } u;
+      u.v = reinterpret_cast<const uint4*>(base)[row * S::C + (c ^ kq)];
+#pragma unroll
+      for (int w = 0; w < S::EPC; ++w) x[c * S::EPC + w] = u.e[w];
+    }
+  } else {
+    load_row<R>(base + row * R, x);
+  }
+}
+
 template <class U>
 __device__ __forceinline__ U umin_(U a, U b) { return a < b ? a : b; }
 template <class U>
@@ -107,60 +164,140 @@ __device__ __forceinline__ void keep_one(U& x, uint32_t& y, U p, uint32_t pv, bo
   }
 }
 
-// Sorts the m = R*T entries held as x[R], y[R] by T participating threads (t = thread
-// index within the group), ascending.  Entries are ord images (+ payloads), so bitwise
-// complement reverses their order: during merge phase k every entry whose index has
-// bit k set is kept complemented, which turns the descending half-merges of Batcher's
-// network into ascending ones and leaves every compare-exchange a plain min/max.
-// s_x / s_y: shared scratch of m entries, used only for exchanges between warps.
-template <bool PAIRS, int R, int T, class U>
-__device__ __forceinline__ void net_sort(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
-  constexpr int M = R * T;
+// One stage of a merge phase: compare-exchange of the entries J apart.  The lower index
+// keeps the minimum (every half-merge runs ascending, see net_sort).
+template <bool PAIRS, int R, int T, int J, class U>
+__device__ __forceinline__ void net_stage(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
+  if constexpr (J < R) {
+    // Both entries of every pair are in this thread.
 #pragma unroll
-  for (int k = 2; k <= M; k <<= 1) {
-    // Entering phase k: flip the entries whose complement state changes.
+    for (int i = 0; i < R; ++i)
+      if ((i & J) == 0) cx_up<PAIRS>(x[i], y[i], x[i | J], y[i | J]);
+  } else if constexpr (J < 32 * R) {
+    // Partner entry: same register of lane t ^ (J / R).
+    constexpr int d = J / R;
+    const bool keep_min = (t & d) == 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const U p = shfl_xor_any(x[i], d);
+      const uint32_t pv = PAIRS ? __shfl_xor_sync(~0u, y[i], d) : 0u;
+      keep_one<PAIRS>(x[i], y[i], p, pv, keep_min);
+    }
+  } else {
+    // Partner in another warp: exchange rows through shared memory.
+    constexpr int d = J / R;
+    const bool keep_min = (t & d) == 0;
+    swz_store_row<R>(s_x, t, x);
+    if constexpr (PAIRS) swz_store_row<R>(s_y, t, y);
+    __syncthreads();
+    U p[R];
+    uint32_t pv[R];
+    swz_load_row<R>(s_x, t ^ d, p);
+    if constexpr (PAIRS) swz_load_row<R>(s_y, t ^ d, pv);
+#pragma unroll
+    for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
+    __syncthreads();
+  }
+}
+
+// Stages J, J/2, ..., 1 of one merge phase.
+template <bool PAIRS, int R, int T, int J, class U>
+__device__ __forceinline__ void net_merge(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
+  if constexpr (J > 0) {
+    net_stage<PAIRS, R, T, J>(x, y, t, s_x, s_y);
+    net_merge<PAIRS, R, T, J / 2>(x, y, t, s_x, s_y);
+  }
+}
+
+// Merge phases K, 2K, ..., M.  Entering phase K, the entries whose complement state
+// changes are flipped: during phase K every entry whose index has bit K set is kept
+// complemented (the last phase, K = M, complements nothing).
+template <bool PAIRS, int R, int T, int K, class U>
+__device__ __forceinline__ void net_phases(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
+  constexpr int M = R * T;
+  if constexpr (K <= M) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int e = t * R + i;
-      const bool before = (k >= 4) && ((e & (k >> 1)) != 0);
-      const bool now = (k < M) && ((e & k) != 0);
+      const bool before = (K >= 4) && ((e & (K >> 1)) != 0);
+      const bool now = (K < M) && ((e & K) != 0);
       const U m = (before != now) ? ~U(0) : U(0);
       x[i] ^= m;
       if constexpr (PAIRS) y[i] ^= (uint32_t)m;
     }
+    net_merge<PAIRS, R, T, K / 2>(x, y, t, s_x, s_y);
+    net_phases<PAIRS, R, T, 2 * K>(x, y, t, s_x, s_y);
+  }
+}
+
+// Phases K, 2K, ..., R of the network on each thread's own R entries (all stages in
+// registers), with the complement states of the full network of R*T entries.
+template <int R, int T, int K, class U>
+__device__ __forceinline__ void net_phases_upto(U (&x)[R], uint32_t (&y)[R], int t) {
+  if constexpr (K <= R) {
+    constexpr int M = R * T;
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < R) {
-        // Both entries of every pair are in this thread.
+    for (int i = 0; i < R; ++i) {
+      const int e = t * R + i;
+      const bool before = (K >= 4) && ((e & (K >> 1)) != 0);
+      const bool now = (K < M) && ((e & K) != 0);
+      x[i] ^= (before != now) ? ~U(0) : U(0);
+    }
+    net_merge<false, R, T, K / 2>(x, y, t, (U*)nullptr, (uint32_t*)nullptr);
+    net_phases_upto<R, T, 2 * K>(x, y, t);
+  }
+}
+
+// Sorts the m = R*T entries held as x[R], y[R] by T participating threads (t = thread
+// index within the group; entry e = t*R + i), ascending: Batcher's bitonic network.
+// Entries are ord images (+ payloads), so bitwise complement reverses their order:
+// keeping the entries of every descending half-merge complemented turns it into an
+// ascending one, and every compare-exchange becomes a plain min/max.  The phases and
+// stages are unrolled by template recursion, so every register index is a constant.
+// s_x / s_y: shared scratch of m entries, used only for exchanges between warps.
+template <bool PAIRS, int R, int T, class U>
+__device__ __forceinline__ void net_sort(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
+  net_phases<PAIRS, R, T, 2>(x, y, t, s_x, s_y);
+}
+
+// The same network with the phases above R in a loop: each such phase is a short run of
+// stages between threads (lane distance d, runtime) followed by the log2(R) register
+// stages, whose code is shared by all phases.  The fully unrolled network for R = 32
+// is tens of thousands of instructions and stalls on instruction fetch; this form
+// keeps one phase body.  Key-only.
+template <int R, int T, class U>
+__device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
+  constexpr int M = R * T;
+  uint32_t none[R];   // payload slots of the shared stage code: never read (key-only)
+  net_phases_upto<R, T, 2, U>(x, none, t);                         // phases 2 .. R
+  for (int k = 2 * R; k <= M; k <<= 1) {
+    // Entering phase k: entries of thread t are complemented while bit k of their index
+    // (bit k/R of t) is set; before, bit k/2 decided.
+    const bool before = (t & (k >> 1) / R) != 0;
+    const bool now = k < M && (t & k / R) != 0;
+    const U m = before != now ? ~U(0) : U(0);
 #pragma unroll
-        for (int i = 0; i < R; ++i)
-          if ((i & j) == 0) cx_up<PAIRS>(x[i], y[i], x[i | j], y[i | j]);
-      } else if (j < 32 * R) {
-        // Partner entry: same register of lane t ^ (j / R); the lower index keeps the min.
-        const int d = j / R;
-        const bool keep_min = (t & d) == 0;
+    for (int i = 0; i < R; ++i) x[i] ^= m;
+    for (int j = k >> 1; j >= R; j >>= 1) {
+      const int d = j / R;
+      const bool keep_min = (t & d) == 0;
+      if (j < 32 * R) {
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           const U p = shfl_xor_any(x[i], d);
-          const uint32_t pv = PAIRS ? __shfl_xor_sync(~0u, y[i], d) : 0u;
-          keep_one<PAIRS>(x[i], y[i], p, pv, keep_min);
+          x[i] = keep_min ? umin_(x[i], p) : umax_(x[i], p);
         }
       } else {
-        // Partner in another warp: exchange rows through shared memory.
-        const int d = j / R;
-        const bool keep_min = (t & d) == 0;
-        store_row<R>(s_x + t * R, x);
-        if constexpr (PAIRS) store_row<R>(s_y + t * R, y);
+        swz_store_row<R>(s_x, t, x);
         __syncthreads();
         U p[R];
-        uint32_t pv[R];
-        load_row<R>(s_x + (t ^ d) * R, p);
-        if constexpr (PAIRS) load_row<R>(s_y + (t ^ d) * R, pv);
+        swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
-        for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
+        for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
         __syncthreads();
       }
     }
+    net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
   }
 }
 
@@ -223,7 +360,100 @@ __global__ void __launch_bounds__(256) k_small_warp(Params P, int p) {
   }
 }
 
-// One 256-thread block per segment of kWarpSortMax+1 .. kMaxSmall keys (list `small`).
+// ---- one warp, or one small group of warps, per small segment ---------------------------
+//
+// Key-only segments of the `small` list are sorted by T = 32 threads (one warp) when
+// they fit 32 x R registers (R <= 32 four-byte or 16 eight-byte keys), and above that
+// by one block of T = 64 (32-bit keys, R <= 32) or T = 128 (64-bit keys, R <= 16)
+// threads up to kMaxSmall keys.  Compared with one
+// 256-thread block and 8 keys per thread, more of the network's stages are register
+// compare-exchanges (with R = 32 only index bits 5 and up need another thread), and a
+// warp needs no block barrier at all.  Keys arrive striped (entry i*T + t: coalesced
+// global reads) and the network holds them blocked (entry t*R + i), so they pass
+// through the swizzled staging array once each way.
+
+// Largest segment one warp sorts: 32 lanes x 32 four-byte or 16 eight-byte keys in
+// registers (0: the 256-thread block kernel sorts every small segment, as for
+// key-value pairs).
+template <class KT, bool PAIRS>
+__host__ __device__ constexpr int small_warp_max() {
+  return PAIRS ? 0 : (sizeof(typename KT::U) == 4 ? 1024 : 512);
+}
+
+template <class KT>
+struct SmallGroup {   // the block that sorts segments above small_warp_max()
+  static constexpr int RMAX = sizeof(typename KT::U) == 4 ? 32 : 16;   // keys per thread
+  static constexpr int T = kMaxSmall / RMAX;
+};
+
+template <class KT, int R, int T>
+__device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, int t,
+                                               typename KT::U* sw) {
+  using U = typename KT::U;
+  using S = RowSwizzle<U, R>;
+  const U* src = (const U*)P.b.key[r.parity] + r.off;
+  U* dst = (U*)P.b.final_key + r.off;
+  const int len = (int)r.len;
+  auto sync = [] { if constexpr (T == 32) __syncwarp(); else __syncthreads(); };
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = i * T + t;
+    sw[S::pos(e)] = e < len ? KT::ord(src[e]) : ~U(0);
+  }
+  sync();
+  U x[R];
+  uint32_t y[R];
+  swz_load_row<R>(sw, t, x);
+  // Exchanges between warps (T > 32) store a thread's own row before a barrier and
+  // read another's after it, so the staging array doubles as their scratch.
+  net_sort_looped<R, T>(x, t, sw);
+  swz_store_row<R>(sw, t, x);
+  sync();
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = i * T + t;
+    if (e < len) dst[e] = KT::unord(sw[S::pos(e)]);
+  }
+  sync();
+}
+
+// Key-only small segments of kWarpSortMax+1 .. small_warp_max() keys (list `small`),
+// one warp each.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
+  using U = typename KT::U;
+  constexpr int kMax = small_warp_max<KT, PAIRS>();
+  static_assert(kMax >= 512, "launched only for key-only sorts");
+  p = level_parity(P, p);
+  __shared__ __align__(16) U s_x[4][kMax];
+  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (unsigned int s = blockIdx.x * 4 + warp; s < count; s += gridDim.x * 4) {
+    const Run r = P.l.small[p][s];
+    if (r.len <= 512) group_sort_run<KT, 512 / 32, 32>(P, r, lane, s_x[warp]);
+    else if constexpr (kMax >= 1024) group_sort_run<KT, 1024 / 32, 32>(P, r, lane, s_x[warp]);
+  }
+}
+
+// Key-only small segments above small_warp_max() (list `group`), one group of
+// SmallGroup::T threads (the whole block) each.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(SmallGroup<KT>::T) k_small_group(Params P, int p) {
+  using U = typename KT::U;
+  using G = SmallGroup<KT>;
+  static_assert(!PAIRS, "launched only for key-only sorts");
+  p = level_parity(P, p);
+  __shared__ __align__(16) U s_x[kMaxSmall];
+  const unsigned int count = min(P.ctrl->lists[p].group, P.l.cap_run);
+  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
+    const Run r = P.l.group[p][s];
+    if (r.len * 2 <= kMaxSmall) group_sort_run<KT, G::RMAX / 2, G::T>(P, r, threadIdx.x, s_x);
+    else group_sort_run<KT, G::RMAX, G::T>(P, r, threadIdx.x, s_x);
+  }
+}
+
+// One 256-thread block per segment of kWarpSortMax+1 .. kMaxSmall keys (list `small`):
+// key-value sorts, and key-only sorts with BQS_OPT_SMALL_SORT = 1.
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_small_block(Params P, int p) {
   using U = typename KT::U;

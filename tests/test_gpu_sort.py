@@ -233,3 +233,35 @@ def test_sort_config1_median_of_3(bqs):
     bqs.set_option("pivot", 0)
     a = inputs.make_keys(1 << 20, "int32", "uniform", seed=0)
     assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="mo3"))
+
+
+# ---- small-segment networks ------------------------------------------------------------------
+
+@pytest.mark.parametrize("small_sort", [0, 1])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_small_networks_every_length(bqs, dtype, small_sort):
+    # Segments of every length 1 .. 2048 (and again for 200 random lengths): each one
+    # goes straight to a network, warp (<= 256), warp (<= 512 / 1024), group or block.
+    import torch
+    bqs.set_option("small_sort", small_sort)
+    rng = inputs.splitmix64(77, 200) % np.uint64(2048)
+    lens = list(range(1, 2049)) + [int(v) + 1 for v in rng]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    for dist in ("uniform", "mod_sqrt", "reversed"):
+        a = inputs.make_keys(int(off[-1]), dtype, dist, seed=small_sort + 1)
+        t = torch.from_numpy(a).cuda()
+        bqs.sort_segmented(t, torch.from_numpy(off).cuda())
+        assert_same_bits(t.cpu().numpy(), oracle.sort_segmented(a, off))
+        st = bqs.stats()
+        assert st["levels"] == 0 and st["small_keys"] == a.size
+
+
+@pytest.mark.parametrize("small_sort", [0, 1])
+@pytest.mark.parametrize("cutoff", [300, 600, 1024, 1500, 2048])
+def test_small_networks_in_full_sorts(bqs, cutoff, small_sort):
+    bqs.set_option("small_sort", small_sort)
+    bqs.set_option("small_cutoff", cutoff)
+    for dtype in DTYPES:
+        a = inputs.make_keys(1_000_003, dtype, "uniform", seed=cutoff)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
