@@ -197,14 +197,40 @@ def _mean_comparisons_per_key(pivot, lg, seeds=3):
     return float(np.mean(out))
 
 
+def _golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")) as f:
+        return json.load(f)
+
+
 def test_median_of_3_comparison_slope():
-    # Average comparisons of median-of-three Quicksort: (12/7) n ln n + O(n), i.e. a
-    # slope of (12/7) ln 2 = 1.188 per unit of log2 n.  A random pivot would give
+    # Average comparisons of median-of-three Quicksort: 1.18 n log2 n + O(n) as the
+    # paper prints it ((12/7) n ln n = 1.188 n log2 n).  A random pivot would give
     # 2 ln 2 = 1.386; a partitioner that compares elements twice would double it.
+    g = _golden()["mo3_comparisons_per_n_log2n"]
     lgs = list(range(14, 22))
     ys = [_mean_comparisons_per_key("mo3", lg) for lg in lgs]
     slope = np.polyfit(lgs, ys, 1)[0]
-    assert abs(slope - 12 / 7 * math.log(2)) < 0.06, slope
+    assert abs(slope - g["value"]) < g["tolerance"], slope
+    assert abs(12 / 7 * math.log(2) - g["value"]) < 0.01
+
+
+def test_insertion_sort_threshold_is_the_papers():
+    m = _golden()["insertion_sort_max_len"]["value"]
+    for n in (m, m + 1):
+        a = inputs.make_keys(n, "int64", "uniform", seed=n)
+        got, c = oracle.sort(a, counters=True)
+        assert np.array_equal(got, np.sort(a))
+        # at most m keys: Insertionsort directly; one more: one partition first
+        assert c["partitions"] == (0 if n == m else 1), (n, c)
+
+
+def test_depth_limit_golden_cases():
+    for n, want in _golden()["depth_limit"]["cases"].items():
+        a = inputs.make_keys(int(n), "int32", "uniform", seed=1)
+        _, c = oracle.sort(a, counters=True)
+        assert c["depth_limit"] == want, (n, c["depth_limit"])
 
 
 def test_median_of_sqrt_comparison_slope():
