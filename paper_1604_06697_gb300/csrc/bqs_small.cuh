@@ -301,6 +301,82 @@ __device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
   }
 }
 
+// 32-bit keys, R = 32: the stages between lanes of one warp (entry bits 5..9) run in
+// registers too, after a transpose of the warp's 32 x 32 block (register i of lane l
+// <-> register l of lane i) through its shared staging rows.  In the transposed layout
+// register i holds entry bits 5..9 = i, so a stage on entry bit 5 + b pairs registers
+// i and i ^ 2^b, the lower index keeping the minimum as everywhere else.  A phase with
+// two or more such stages pays two transposes (80 shared-memory accesses per thread,
+// conflict-free) instead of one shuffle and three ALU operations per key and stage.
+
+// Transposes a warp's 32 x 32 block: afterwards x[i] of lane l is the entry that was
+// x[l] of lane i.  wb: the warp's 1024-word swizzled staging rows.
+__device__ __forceinline__ void warp_transpose32(uint32_t (&x)[32], int lane, uint32_t* wb) {
+  using S = RowSwizzle<uint32_t, 32>;
+  swz_store_row<32>(wb, lane, x);                         // row `lane`, 16-byte chunks
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = wb[S::pos(i * 32 + lane)];   // column `lane`
+  __syncwarp();
+}
+
+// Register stages 2^(nb-1), ..., 2, 1 (nb in 1..5) of a transposed block.
+__device__ __forceinline__ void transposed_stages(uint32_t (&x)[32], int nb) {
+  uint32_t none[32];   // payload slots of the shared stage code: never read (key-only)
+  switch (nb) {
+    case 5: net_stage<false, 32, 1, 16>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    case 4: net_stage<false, 32, 1, 8>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    case 3: net_stage<false, 32, 1, 4>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    case 2: net_stage<false, 32, 1, 2>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    default: net_stage<false, 32, 1, 1>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, uint32_t* s_x) {
+  constexpr int R = 32, M = R * T;
+  uint32_t none[R];
+  const int lane = t & 31;
+  uint32_t* wb = s_x + (t >> 5) * 1024;
+  net_phases_upto<R, T, 2, uint32_t>(x, none, t);                  // phases 2 .. 32
+  for (int k = 2 * R; k <= M; k <<= 1) {
+    const bool before = (t & (k >> 1) / R) != 0;
+    const bool now = k < M && (t & k / R) != 0;
+    const uint32_t m = before != now ? ~0u : 0u;
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] ^= m;
+    int j = k >> 1;
+    for (; j >= 32 * R; j >>= 1) {                // between warps: shared-memory rows
+      const int d = j / R;
+      const bool keep_min = (t & d) == 0;
+      swz_store_row<R>(s_x, t, x);
+      __syncthreads();
+      uint32_t p[R];
+      swz_load_row<R>(s_x, t ^ d, p);
+#pragma unroll
+      for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
+      __syncthreads();
+    }
+    if (j == R) {                                 // one lane stage: a shuffle
+      const bool keep_min = (t & 1) == 0;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const uint32_t p = __shfl_xor_sync(~0u, x[i], 1);
+        x[i] = keep_min ? umin_(x[i], p) : umax_(x[i], p);
+      }
+    } else {                                      // stages j .. R: transposed
+      warp_transpose32(x, lane, wb);
+      transposed_stages(x, 31 - __clz(j / R) + 1);
+      warp_transpose32(x, lane, wb);
+    }
+    net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
+  }
+}
+
 // Loads len keys of one segment (ord images, padded with the largest key) into the
 // group's registers, entry e = t*R + i, through shared memory so that global reads are
 // coalesced; sorts; writes the first len entries back (raw keys) the same way.
@@ -406,7 +482,8 @@ __device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, in
   swz_load_row<R>(sw, t, x);
   // Exchanges between warps (T > 32) store a thread's own row before a barrier and
   // read another's after it, so the staging array doubles as their scratch.
-  net_sort_looped<R, T>(x, t, sw);
+  if constexpr (sizeof(U) == 4 && R == 32) net_sort_transposed<T>(x, t, sw);
+  else net_sort_looped<R, T>(x, t, sw);
   swz_store_row<R>(sw, t, x);
   sync();
 #pragma unroll
@@ -438,7 +515,7 @@ __global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
 // Key-only small segments above small_warp_max() (list `group`), one group of
 // SmallGroup::T threads (the whole block) each.
 template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(SmallGroup<KT>::T) k_small_group(Params P, int p) {
+__global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<KT>::T)) k_small_group(Params P, int p) {
   using U = typename KT::U;
   using G = SmallGroup<KT>;
   static_assert(!PAIRS, "launched only for key-only sorts");
