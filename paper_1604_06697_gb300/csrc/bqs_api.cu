@@ -21,7 +21,17 @@ int64_t g_ws_bytes = 0;
 thread_local Stats t_stats;
 thread_local char t_err[320];
 thread_local Ctrl* t_pinned = nullptr;
-thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
+// Events belong to the device that was current when they were created, so the
+// per-thread caches are kept per device.
+constexpr int kMaxDevices = 64;
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events[kMaxDevices];
+thread_local cudaEvent_t t_counts_event[kMaxDevices];
+
+int current_device_slot() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+  return dev >= 0 && dev < kMaxDevices ? dev : 0;
+}
 
 Options snapshot_options() {
   std::lock_guard<std::mutex> g(g_opt_mu);
@@ -99,7 +109,18 @@ Ctrl* pinned_ctrl() {
   return t_pinned;
 }
 
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() { return t_events; }
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() {
+  return t_events[current_device_slot()];
+}
+
+cudaEvent_t counts_event() {
+  cudaEvent_t& e = t_counts_event[current_device_slot()];
+  if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
 
 }  // namespace bqs
 

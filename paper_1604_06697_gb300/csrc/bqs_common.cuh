@@ -154,6 +154,11 @@ struct Params {
   int group_min;        // small segments longer than this go to the `group` list
 };
 
+__device__ __forceinline__ void clear_counts(ListCounts* l) {
+  l->large = 0; l->fill = 0; l->large_keys = 0;
+  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0; l->group = 0;
+}
+
 // Parity of the lists the current level consumes: given by the host when it drives
 // the level loop, read from the control block when the loop runs on the device.
 __device__ __forceinline__ int level_parity(const Params& P, int host_p) {

@@ -287,7 +287,10 @@ struct LevelRing {
 };
 
 inline LevelRing& level_ring() {
-  static thread_local LevelRing r;
+  static thread_local LevelRing rings[64];   // per device: events belong to one device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); dev = 0; }
+  LevelRing& r = rings[dev];
   if (!r.ok) {
     void* p = nullptr;
     if (cudaMallocHost(&p, 8 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return r; }
@@ -492,6 +495,7 @@ int run_call(const Call& c, Stats& st) {
   BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
 
   ListCounts cur{};
+  bool host_fresh = false;   // `host` holds this call's control block
   if (device_loop) {
     if (c.seg_offsets) {
       const int g = (int)std::min<int64_t>((c.nseg + 255) / 256, 4 * sm_count());
@@ -533,6 +537,7 @@ int run_call(const Call& c, Stats& st) {
     BQS_CK(cudaStreamSynchronize(s));
     if (host->status) return status_code(host->status);
     cur = host->lists[0];
+    host_fresh = true;
   } else {
     k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
     st.kernel_launches += 1;
@@ -558,6 +563,10 @@ int run_call(const Call& c, Stats& st) {
   // Every level removes the pivot class of each segment, and past the depth limit the
   // range-midpoint pivot halves the key range: more levels than this means a bug.
   const int max_levels = P.depth_limit + 8 * (int)sizeof(U) + 40;
+  // Sorts read each level's counts behind an event right after its bookkeeping;
+  // partitions and the allocation-free entry point (which creates no CUDA objects)
+  // synchronise the stream at the end of each level instead.
+  const cudaEvent_t counts_ev = (c.partition_only || c.fixed_ws) ? nullptr : counts_event();
   for (int level = 0;; ++level) {
     if (level > max_levels) return kErrInternal;
     P.p = level & 1;
@@ -566,8 +575,6 @@ int run_call(const Call& c, Stats& st) {
       st.levels += 1;
       st.partition_launches += 1;
       st.active_keys += (int64_t)cur.large_keys;
-      // The counters of the lists this level produces start at zero.
-      BQS_CK(cudaMemsetAsync(&P.ctrl->lists[P.p ^ 1], 0, sizeof(ListCounts), s));
       if (cur.todo) {
         k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(cur.todo, 8 * sms), 256, 0, s>>>(P);
         st.kernel_launches += 1;
@@ -589,6 +596,13 @@ int run_call(const Call& c, Stats& st) {
       P.test_stall = 0;
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
+      if (counts_ev) {
+        // The next level's counts are final once the bookkeeping has run: read them
+        // back now, while this level's fills and sorting networks still run, so the
+        // host enqueues the next level before the stream drains.
+        BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        BQS_CK(cudaEventRecord(counts_ev, s));
+      }
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 3;
     }
@@ -608,8 +622,13 @@ int run_call(const Call& c, Stats& st) {
     }
     BQS_CK(cudaGetLastError());
     if (!nlarge) break;
-    BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    BQS_CK(cudaStreamSynchronize(s));
+    if (counts_ev) {
+      BQS_CK(cudaEventSynchronize(counts_ev));
+    } else {
+      BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      BQS_CK(cudaStreamSynchronize(s));
+    }
+    host_fresh = true;
     if (host->status) return status_code(host->status);
     if (c.partition_only) {
       // split = #(< pivot); the cursor of the single segment holds it.
@@ -621,11 +640,18 @@ int run_call(const Call& c, Stats& st) {
     }
     cur = host->lists[P.p ^ 1];
   }
-  st.moved_keys = (int64_t)host->moved_keys;
-  st.equal_keys = (int64_t)host->equal_keys;
-  st.small_keys = (int64_t)host->small_keys;
-  st.local_keys = (int64_t)host->local_keys;
-  st.fallback_pivots = (int64_t)host->fallbacks;
+  if (host_fresh) {
+    st.moved_keys = (int64_t)host->moved_keys;
+    st.equal_keys = (int64_t)host->equal_keys;
+    st.small_keys = (int64_t)host->small_keys;
+    st.local_keys = (int64_t)host->local_keys;
+    st.fallback_pivots = (int64_t)host->fallbacks;
+  } else if (!c.partition_only) {
+    // A single array that went straight to a network or the single-block sort:
+    // nothing was read back, and the counts follow from where it was routed.
+    st.small_keys = (cur.tiny | cur.small | cur.group) ? c.n : 0;
+    st.local_keys = cur.local ? c.n : 0;
+  }
   st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
   if (timing && ev_used) {
     BQS_CK(cudaStreamSynchronize(s));

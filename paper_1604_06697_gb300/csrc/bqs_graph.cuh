@@ -9,11 +9,6 @@
 
 namespace bqs {
 
-__device__ __forceinline__ void clear_counts(ListCounts* l) {
-  l->large = 0; l->fill = 0; l->large_keys = 0;
-  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0; l->group = 0;
-}
-
 // First kernel of a level: the lists this level produces start empty.  After an error
 // (levels enqueued ahead of the host's check) the level's own lists are emptied too,
 // so every later kernel of the call finds no work.

@@ -67,7 +67,8 @@ int64_t layout_bytes(int64_t n, int key_size, bool pairs, int64_t nseg, int smal
 void user_workspace(void** ptr, int64_t* bytes);
 void prepare_mempool();
 Ctrl* pinned_ctrl();
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();   // of the current device
+cudaEvent_t counts_event();     // the calling thread's, on the current device (null on failure)
 
 // Implemented in the per-dtype translation units.
 int run_i32(const Call& c, Stats& st);

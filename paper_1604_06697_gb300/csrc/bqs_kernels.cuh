@@ -9,6 +9,7 @@
 #pragma once
 
 #include "bqs_common.cuh"
+#include "bqs_network.cuh"
 
 namespace bqs {
 
@@ -267,9 +268,10 @@ __device__ void block_bitonic_sort(U* k, uint32_t* v, int m) {
 
 // ---- pivot selection kernel ---------------------------------------------------------------
 
-// One block per large segment whose pivot needs the whole block (the list `todo`):
+// Pivots that need more than one thread (the list `todo`):
 //  * sqrt rule (Sec. 4) at 20000 keys and more: the median of k = floor(sqrt(len))|1
-//    equally spaced keys (k capped at kMaxSample), sorted in shared memory;
+//    equally spaced keys (k capped at kMaxSample); samples of up to 256 keys are
+//    sorted in registers by one warp each, larger ones in shared memory by one block;
 //  * a segment at the depth limit gets the midpoint of its ord-key range (payload
 //    range when all its keys are equal): each such level halves the range, so the
 //    recursion depth stays bounded by the key width (the role Heapsort plays in Sec. 2).
@@ -286,9 +288,60 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   const int pp = level_parity(P, P.p);
   const unsigned int count = min(P.ctrl->lists[pp].todo, P.l.cap_large);
   Seg* segs = P.l.large[pp];
+  auto sample_size = [](int64_t len) {
+    const int64_t k = isqrt64(len) | 1;
+    return k > kMaxSample ? (int64_t)kMaxSample : k;
+  };
+
+  // Samples of up to 256 keys: one warp per segment sorts them in registers (8 per
+  // lane, a bitonic network without block barriers) and reads off the median.
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned int nw = blockDim.x >> 5;
+    for (unsigned int i = blockIdx.x * nw + warp; i < count; i += gridDim.x * nw) {
+      const unsigned int s = P.l.todo[pp][i];
+      const Seg sg = segs[s];
+      if (sg.depth >= P.depth_limit) continue;
+      const int64_t k = sample_size(sg.len);
+      if (k > 256) continue;
+      const U* keys = (const U*)P.b.key[sg.parity];
+      const uint32_t* vals = P.b.val[sg.parity];
+      U x[8];
+      uint32_t y[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int e = lane * 8 + r;
+        if (e < k) {
+          const int64_t pos = sg.off + ((2 * (int64_t)e + 1) * sg.len) / (2 * k);
+          x[r] = KT::ord(keys[pos]);
+          y[r] = PAIRS ? vals[pos] : 0u;
+        } else {
+          x[r] = ~U(0);
+          y[r] = 0xFFFFFFFFu;
+        }
+      }
+      net_sort<PAIRS, 8, 32>(x, y, lane, (U*)nullptr, (uint32_t*)nullptr);
+      const int med = (int)((k - 1) / 2);
+      U mk = x[0];
+      uint32_t mv = y[0];
+#pragma unroll
+      for (int r = 1; r < 8; ++r)
+        if (r == (med & 7)) { mk = x[r]; mv = y[r]; }
+      if constexpr (sizeof(U) == 8) mk = (U)__shfl_sync(~0u, (unsigned long long)mk, med >> 3);
+      else mk = (U)__shfl_sync(~0u, (unsigned)mk, med >> 3);
+      mv = __shfl_sync(~0u, mv, med >> 3);
+      if (lane == 0) {
+        segs[s].pkey = (uint64_t)KT::unord(mk);
+        segs[s].pval = PAIRS ? mv : 0u;
+      }
+    }
+  }
+
+  // Larger samples and the depth-limit fallback: one block per segment.
   for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
     const unsigned int s = P.l.todo[pp][i];
     const Seg sg = segs[s];
+    if (sg.depth < P.depth_limit && sample_size(sg.len) <= 256) continue;   // done above
     const U* keys = (const U*)P.b.key[sg.parity];
     const uint32_t* vals = P.b.val[sg.parity];
     const int64_t b = sg.off, len = sg.len;
@@ -338,8 +391,7 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
       }
       if (threadIdx.x == 0) atomicAdd(&P.ctrl->fallbacks, 1ull);
     } else {
-      int64_t k = isqrt64(len) | 1;
-      if (k > kMaxSample) k = kMaxSample;
+      const int64_t k = sample_size(len);
       const int m = next_pow2((int)k);
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
         if (i < k) {

@@ -1,381 +1,15 @@
-// Small-segment sort: a bitonic sorting network (Batcher 1968) held in registers.
-//
-// This is the GPU stand-in for the Insertionsort that finishes the paper's recursion
-// (Sec. 2, "switch to Insertionsort ... when the array size is less than 16"): a
-// segment of at most the small-segment cutoff is loaded into shared memory, padded
-// with the largest order key to m = 2^k entries, and sorted by a fixed network with no
-// data-dependent branches.  Each thread holds R consecutive entries in registers
-// (entry e = thread * R + i), so
-//   * exchanges between entries less than R apart are register compare-exchanges,
-//   * exchanges between threads of one warp use __shfl_xor_sync,
-//   * only exchanges between warps go through shared memory.
-// Segments of at most 256 keys are sorted by one warp each (k_small_warp); longer ones
-// by one 256-thread block each (k_small_block).
+// Small-segment sort: the GPU stand-in for the Insertionsort that finishes the paper's
+// recursion (Sec. 2, "switch to Insertionsort ... when the array size is less than
+// 16"): a segment of at most the small-segment cutoff is sorted by one of the register
+// networks of bqs_network.cuh.  Segments of at most 256 keys: one warp each
+// (k_small_warp); longer key-only segments: one warp (k_small_warps) or one small warp
+// group (k_small_group) each; key-value segments: one 256-thread block each
+// (k_small_block).
 #pragma once
 
 #include "bqs_kernels.cuh"
 
 namespace bqs {
-
-template <class U>
-__device__ __forceinline__ U shfl_xor_any(U x, int d) {
-  if constexpr (sizeof(U) == 8) {
-    return (U)__shfl_xor_sync(~0u, (unsigned long long)x, d);
-  } else {
-    return (U)__shfl_xor_sync(~0u, (unsigned)x, d);
-  }
-}
-
-// A thread's row of R consecutive entries in shared memory, moved with 16-byte (or
-// 8-byte) accesses: a warp then touches consecutive 16-byte words and no bank twice
-// beyond the minimum number of wavefronts.
-template <int R, class U>
-__device__ __forceinline__ void store_row(U* dst, const U (&x)[R]) {
-  constexpr int BYTES = R * (int)sizeof(U);
-  if constexpr (BYTES % 16 == 0) {
-    constexpr int PER = 16 / (int)sizeof(U);
-#pragma unroll
-    for (int c = 0; c < BYTES / 16; ++c) {
-      union { uint4 v; U e[PER]; } u;
-#pragma unroll
-      for (int e = 0; e < PER; ++e) u.e[e] = x[c * PER + e];
-      reinterpret_cast<uint4*>(dst)[c] = u.v;
-    }
-  } else if constexpr (BYTES == 8) {
-    union { uint2 v; U e[8 / sizeof(U)]; } u;
-#pragma unroll
-    for (int e = 0; e < R; ++e) u.e[e] = x[e];
-    *reinterpret_cast<uint2*>(dst) = u.v;
-  } else {
-#pragma unroll
-    for (int e = 0; e < R; ++e) dst[e] = x[e];
-  }
-}
-
-template <int R, class U>
-__device__ __forceinline__ void load_row(const U* src, U (&x)[R]) {
-  constexpr int BYTES = R * (int)sizeof(U);
-  if constexpr (BYTES % 16 == 0) {
-    constexpr int PER = 16 / (int)sizeof(U);
-#pragma unroll
-    for (int c = 0; c < BYTES / 16; ++c) {
-      union { uint4 v; U e[PER]; } u;
-      u.v = reinterpret_cast<const uint4*>(src)[c];
-#pragma unroll
-      for (int e = 0; e < PER; ++e) x[c * PER + e] = u.e[e];
-    }
-  } else if constexpr (BYTES == 8) {
-    union { uint2 v; U e[8 / sizeof(U)]; } u;
-    u.v = *reinterpret_cast<const uint2*>(src);
-#pragma unroll
-    for (int e = 0; e < R; ++e) x[e] = u.e[e];
-  } else {
-#pragma unroll
-    for (int e = 0; e < R; ++e) x[e] = src[e];
-  }
-}
-
-constexpr int ilog2_c(int v) { return v <= 1 ? 0 : 1 + ilog2_c(v >> 1); }
-
-// Staging layout for rows of R entries (row t = the entries thread t holds).  Entry e
-// of row e / R lives at pos(e): its 16-byte chunk index within the row is XORed with
-// key(row).  Then 16-byte row accesses by 8 consecutive threads (one shared-memory
-// wavefront) touch 8 different bank groups, and striped accesses (entry i*T + t by
-// thread t: coalesced with global memory) by a warp, or a half warp for 8-byte keys,
-// XOR their chunk index with one constant, which keeps their banks distinct.  Rows
-// shorter than one chunk are left unswizzled.
-template <class U, int R>
-struct RowSwizzle {
-  static constexpr int EPC = 16 / (int)sizeof(U);        // entries per 16-byte chunk
-  static constexpr bool kChunked = R >= EPC;
-  static constexpr int C = kChunked ? R / EPC : 1;        // chunks per row
-  static constexpr int LOGC = ilog2_c(C);
-  __device__ static __forceinline__ int key(int row) {
-    if constexpr (!kChunked) return 0;
-    else if constexpr (LOGC >= 3) return row & 7;
-    else return (row >> (3 - LOGC)) & (C - 1);
-  }
-  __device__ static __forceinline__ int pos(int e) { return e ^ (key(e / R) * EPC); }
-};
-
-template <int R, class U>
-__device__ __forceinline__ void swz_store_row(U* base, int row, const U (&x)[R]) {
-  using S = RowSwizzle<U, R>;
-  if constexpr (S::kChunked) {
-    const int kq = S::key(row);
-#pragma unroll
-    for (int c = 0; c < S::C; ++c) {
-      union { uint4 v; U e[S::EPC]; } u;
-#pragma unroll
-      for (int w = 0; w < S::EPC; ++w) u.e[w] = x[c * S::EPC + w];
-      reinterpret_cast<uint4*>(base)[row * S::C + (c ^ kq)] = u.v;
-    }
-  } else {
-    store_row<R>(base + row * R, x);
-  }
-}
-
-template <int R, class U>
-__device__ __forceinline__ void swz_load_row(const U* base, int row, U (&x)[R]) {
-  using S = RowSwizzle<U, R>;
-  if constexpr (S::kChunked) {
-    const int kq = S::key(row);
-#pragma unroll
-    for (int c = 0; c < S::C; ++c) {
-      union { uint4 v; U e[S::EPC]; } u;
-      u.v = reinterpret_cast<const uint4*>(base)[row * S::C + (c ^ kq)];
-#pragma unroll
-      for (int w = 0; w < S::EPC; ++w) x[c * S::EPC + w] = u.e[w];
-    }
-  } else {
-    load_row<R>(base + row * R, x);
-  }
-}
-
-template <class U>
-__device__ __forceinline__ U umin_(U a, U b) { return a < b ? a : b; }
-template <class U>
-__device__ __forceinline__ U umax_(U a, U b) { return a < b ? b : a; }
-
-// Ascending compare-exchange of two register entries: afterwards a <= b.
-template <bool PAIRS, class U>
-__device__ __forceinline__ void cx_up(U& a, uint32_t& va, U& b, uint32_t& vb) {
-  if constexpr (PAIRS) {
-    const bool sw = elem_less<PAIRS>(b, vb, a, va);
-    const U ta = sw ? b : a, tb = sw ? a : b;
-    const uint32_t tva = sw ? vb : va, tvb = sw ? va : vb;
-    a = ta; b = tb; va = tva; vb = tvb;
-  } else {
-    const U lo = umin_(a, b), hi = umax_(a, b);
-    a = lo;
-    b = hi;
-  }
-}
-
-// Keeps the smaller (keep_min) or larger of an entry and its partner's.
-template <bool PAIRS, class U>
-__device__ __forceinline__ void keep_one(U& x, uint32_t& y, U p, uint32_t pv, bool keep_min) {
-  if constexpr (PAIRS) {
-    const bool take = elem_less<PAIRS>(p, pv, x, y) == keep_min;
-    x = take ? p : x;
-    y = take ? pv : y;
-  } else {
-    x = keep_min ? umin_(x, p) : umax_(x, p);
-  }
-}
-
-// One stage of a merge phase: compare-exchange of the entries J apart.  The lower index
-// keeps the minimum (every half-merge runs ascending, see net_sort).
-template <bool PAIRS, int R, int T, int J, class U>
-__device__ __forceinline__ void net_stage(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
-  if constexpr (J < R) {
-    // Both entries of every pair are in this thread.
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-      if ((i & J) == 0) cx_up<PAIRS>(x[i], y[i], x[i | J], y[i | J]);
-  } else if constexpr (J < 32 * R) {
-    // Partner entry: same register of lane t ^ (J / R).
-    constexpr int d = J / R;
-    const bool keep_min = (t & d) == 0;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const U p = shfl_xor_any(x[i], d);
-      const uint32_t pv = PAIRS ? __shfl_xor_sync(~0u, y[i], d) : 0u;
-      keep_one<PAIRS>(x[i], y[i], p, pv, keep_min);
-    }
-  } else {
-    // Partner in another warp: exchange rows through shared memory.
-    constexpr int d = J / R;
-    const bool keep_min = (t & d) == 0;
-    swz_store_row<R>(s_x, t, x);
-    if constexpr (PAIRS) swz_store_row<R>(s_y, t, y);
-    __syncthreads();
-    U p[R];
-    uint32_t pv[R];
-    swz_load_row<R>(s_x, t ^ d, p);
-    if constexpr (PAIRS) swz_load_row<R>(s_y, t ^ d, pv);
-#pragma unroll
-    for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
-    __syncthreads();
-  }
-}
-
-// Stages J, J/2, ..., 1 of one merge phase.
-template <bool PAIRS, int R, int T, int J, class U>
-__device__ __forceinline__ void net_merge(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
-  if constexpr (J > 0) {
-    net_stage<PAIRS, R, T, J>(x, y, t, s_x, s_y);
-    net_merge<PAIRS, R, T, J / 2>(x, y, t, s_x, s_y);
-  }
-}
-
-// Merge phases K, 2K, ..., M.  Entering phase K, the entries whose complement state
-// changes are flipped: during phase K every entry whose index has bit K set is kept
-// complemented (the last phase, K = M, complements nothing).
-template <bool PAIRS, int R, int T, int K, class U>
-__device__ __forceinline__ void net_phases(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
-  constexpr int M = R * T;
-  if constexpr (K <= M) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const int e = t * R + i;
-      const bool before = (K >= 4) && ((e & (K >> 1)) != 0);
-      const bool now = (K < M) && ((e & K) != 0);
-      const U m = (before != now) ? ~U(0) : U(0);
-      x[i] ^= m;
-      if constexpr (PAIRS) y[i] ^= (uint32_t)m;
-    }
-    net_merge<PAIRS, R, T, K / 2>(x, y, t, s_x, s_y);
-    net_phases<PAIRS, R, T, 2 * K>(x, y, t, s_x, s_y);
-  }
-}
-
-// Phases K, 2K, ..., R of the network on each thread's own R entries (all stages in
-// registers), with the complement states of the full network of R*T entries.
-template <int R, int T, int K, class U>
-__device__ __forceinline__ void net_phases_upto(U (&x)[R], uint32_t (&y)[R], int t) {
-  if constexpr (K <= R) {
-    constexpr int M = R * T;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const int e = t * R + i;
-      const bool before = (K >= 4) && ((e & (K >> 1)) != 0);
-      const bool now = (K < M) && ((e & K) != 0);
-      x[i] ^= (before != now) ? ~U(0) : U(0);
-    }
-    net_merge<false, R, T, K / 2>(x, y, t, (U*)nullptr, (uint32_t*)nullptr);
-    net_phases_upto<R, T, 2 * K>(x, y, t);
-  }
-}
-
-// Sorts the m = R*T entries held as x[R], y[R] by T participating threads (t = thread
-// index within the group; entry e = t*R + i), ascending: Batcher's bitonic network.
-// Entries are ord images (+ payloads), so bitwise complement reverses their order:
-// keeping the entries of every descending half-merge complemented turns it into an
-// ascending one, and every compare-exchange becomes a plain min/max.  The phases and
-// stages are unrolled by template recursion, so every register index is a constant.
-// s_x / s_y: shared scratch of m entries, used only for exchanges between warps.
-template <bool PAIRS, int R, int T, class U>
-__device__ __forceinline__ void net_sort(U (&x)[R], uint32_t (&y)[R], int t, U* s_x, uint32_t* s_y) {
-  net_phases<PAIRS, R, T, 2>(x, y, t, s_x, s_y);
-}
-
-// The same network with the phases above R in a loop: each such phase is a short run of
-// stages between threads (lane distance d, runtime) followed by the log2(R) register
-// stages, whose code is shared by all phases.  The fully unrolled network for R = 32
-// is tens of thousands of instructions and stalls on instruction fetch; this form
-// keeps one phase body.  Key-only.
-template <int R, int T, class U>
-__device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
-  constexpr int M = R * T;
-  uint32_t none[R];   // payload slots of the shared stage code: never read (key-only)
-  net_phases_upto<R, T, 2, U>(x, none, t);                         // phases 2 .. R
-  for (int k = 2 * R; k <= M; k <<= 1) {
-    // Entering phase k: entries of thread t are complemented while bit k of their index
-    // (bit k/R of t) is set; before, bit k/2 decided.
-    const bool before = (t & (k >> 1) / R) != 0;
-    const bool now = k < M && (t & k / R) != 0;
-    const U m = before != now ? ~U(0) : U(0);
-#pragma unroll
-    for (int i = 0; i < R; ++i) x[i] ^= m;
-    for (int j = k >> 1; j >= R; j >>= 1) {
-      const int d = j / R;
-      const bool keep_min = (t & d) == 0;
-      if (j < 32 * R) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const U p = shfl_xor_any(x[i], d);
-          x[i] = keep_min ? umin_(x[i], p) : umax_(x[i], p);
-        }
-      } else {
-        swz_store_row<R>(s_x, t, x);
-        __syncthreads();
-        U p[R];
-        swz_load_row<R>(s_x, t ^ d, p);
-#pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-        __syncthreads();
-      }
-    }
-    net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
-  }
-}
-
-// 32-bit keys, R = 32: the stages between lanes of one warp (entry bits 5..9) run in
-// registers too, after a transpose of the warp's 32 x 32 block (register i of lane l
-// <-> register l of lane i) through its shared staging rows.  In the transposed layout
-// register i holds entry bits 5..9 = i, so a stage on entry bit 5 + b pairs registers
-// i and i ^ 2^b, the lower index keeping the minimum as everywhere else.  A phase with
-// two or more such stages pays two transposes (80 shared-memory accesses per thread,
-// conflict-free) instead of one shuffle and three ALU operations per key and stage.
-
-// Transposes a warp's 32 x 32 block: afterwards x[i] of lane l is the entry that was
-// x[l] of lane i.  wb: the warp's 1024-word swizzled staging rows.
-__device__ __forceinline__ void warp_transpose32(uint32_t (&x)[32], int lane, uint32_t* wb) {
-  using S = RowSwizzle<uint32_t, 32>;
-  swz_store_row<32>(wb, lane, x);                         // row `lane`, 16-byte chunks
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = wb[S::pos(i * 32 + lane)];   // column `lane`
-  __syncwarp();
-}
-
-// Register stages 2^(nb-1), ..., 2, 1 (nb in 1..5) of a transposed block.
-__device__ __forceinline__ void transposed_stages(uint32_t (&x)[32], int nb) {
-  uint32_t none[32];   // payload slots of the shared stage code: never read (key-only)
-  switch (nb) {
-    case 5: net_stage<false, 32, 1, 16>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
-      [[fallthrough]];
-    case 4: net_stage<false, 32, 1, 8>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
-      [[fallthrough]];
-    case 3: net_stage<false, 32, 1, 4>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
-      [[fallthrough]];
-    case 2: net_stage<false, 32, 1, 2>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
-      [[fallthrough]];
-    default: net_stage<false, 32, 1, 1>(x, none, 0, (uint32_t*)nullptr, (uint32_t*)nullptr);
-  }
-}
-
-template <int T>
-__device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, uint32_t* s_x) {
-  constexpr int R = 32, M = R * T;
-  uint32_t none[R];
-  const int lane = t & 31;
-  uint32_t* wb = s_x + (t >> 5) * 1024;
-  net_phases_upto<R, T, 2, uint32_t>(x, none, t);                  // phases 2 .. 32
-  for (int k = 2 * R; k <= M; k <<= 1) {
-    const bool before = (t & (k >> 1) / R) != 0;
-    const bool now = k < M && (t & k / R) != 0;
-    const uint32_t m = before != now ? ~0u : 0u;
-#pragma unroll
-    for (int i = 0; i < R; ++i) x[i] ^= m;
-    int j = k >> 1;
-    for (; j >= 32 * R; j >>= 1) {                // between warps: shared-memory rows
-      const int d = j / R;
-      const bool keep_min = (t & d) == 0;
-      swz_store_row<R>(s_x, t, x);
-      __syncthreads();
-      uint32_t p[R];
-      swz_load_row<R>(s_x, t ^ d, p);
-#pragma unroll
-      for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-      __syncthreads();
-    }
-    if (j == R) {                                 // one lane stage: a shuffle
-      const bool keep_min = (t & 1) == 0;
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const uint32_t p = __shfl_xor_sync(~0u, x[i], 1);
-        x[i] = keep_min ? umin_(x[i], p) : umax_(x[i], p);
-      }
-    } else {                                      // stages j .. R: transposed
-      warp_transpose32(x, lane, wb);
-      transposed_stages(x, 31 - __clz(j / R) + 1);
-      warp_transpose32(x, lane, wb);
-    }
-    net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
-  }
-}
 
 // Loads len keys of one segment (ord images, padded with the largest key) into the
 // group's registers, entry e = t*R + i, through shared memory so that global reads are

@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pp = level_parity(P, P.p);
+  // The lists this level's bookkeeping fills (after this kernel) start empty.
+  if (blockIdx.x == 0 && threadIdx.x == 0) clear_counts(&P.ctrl->lists[pp ^ 1]);
   const unsigned long long lc = P.ctrl->lists[pp].large;
   const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
   const Seg* __restrict__ segs = P.l.large[pp];

@@ -265,3 +265,16 @@ def test_small_networks_in_full_sorts(bqs, cutoff, small_sort):
     for dtype in DTYPES:
         a = inputs.make_keys(1_000_003, dtype, "uniform", seed=cutoff)
         assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+
+
+def test_statistics_of_a_sort_without_partition_levels(bqs):
+    # A sort that never partitions reads nothing back; its statistics must still be
+    # its own, not the previous call's.
+    gpu_sort(bqs, inputs.make_keys(1 << 20, "int32", "uniform", seed=1))
+    assert bqs.stats()["moved_keys"] > 0
+    for n in (100, 1000, 2048):
+        a = inputs.make_keys(n, "int64", "uniform", seed=n)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+        st = bqs.stats()
+        assert st["levels"] == 0 and st["moved_keys"] == 0 and st["equal_keys"] == 0
+        assert st["small_keys"] == n and st["local_keys"] == 0
