@@ -376,4 +376,82 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
   }
 }
 
+// 64-bit keys, R = 16: entry bits 0..3 are register bits and 4..8 lane bits.  Each
+// half warp transposes its 16 x 16 block (register i of lane l <-> register l of lane
+// i within the half), which brings entry bits 4..7 into the registers; bit 8 (lane
+// bit 4) stays a shuffle with the other half warp, bits above a shared-memory
+// exchange between warps.  Each half warp's block is 2 KB of swizzled staging rows.
+
+__device__ __forceinline__ void halfwarp_transpose16(uint64_t (&x)[16], int lane, uint64_t* wb) {
+  using S = RowSwizzle<uint64_t, 16>;
+  swz_store_row<16>(wb, lane, x);                          // row `lane` of the warp's 32
+  __syncwarp();
+  const int h = lane & 16, c = lane & 15;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = wb[S::pos((h + i) * 16 + c)];   // column c of the half
+  __syncwarp();
+}
+
+// Register stages 2^(nb-1), ..., 1 (nb in 1..4) of a transposed 16-entry row.
+__device__ __forceinline__ void transposed_stages16(uint64_t (&x)[16], int nb) {
+  uint32_t none[16];   // payload slots of the shared stage code: never read (key-only)
+  switch (nb) {
+    case 4: net_stage<false, 16, 1, 8>(x, none, 0, (uint64_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    case 3: net_stage<false, 16, 1, 4>(x, none, 0, (uint64_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    case 2: net_stage<false, 16, 1, 2>(x, none, 0, (uint64_t*)nullptr, (uint32_t*)nullptr);
+      [[fallthrough]];
+    default: net_stage<false, 16, 1, 1>(x, none, 0, (uint64_t*)nullptr, (uint32_t*)nullptr);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void net_sort_transposed64(uint64_t (&x)[16], int t, uint64_t* s_x) {
+  constexpr int R = 16, M = R * T;
+  uint32_t none[R];
+  const int lane = t & 31;
+  uint64_t* wb = s_x + (t >> 5) * 512;
+  auto lane_stage = [&](int d) {
+    const bool keep_min = (t & d) == 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const uint64_t p = __shfl_xor_sync(~0u, (unsigned long long)x[i], d);
+      x[i] = keep_min ? umin_(x[i], p) : umax_(x[i], p);
+    }
+  };
+  net_phases_upto<R, T, 2, uint64_t>(x, none, t);                  // phases 2 .. 16
+  for (int k = 2 * R; k <= M; k <<= 1) {
+    const bool before = (t & (k >> 1) / R) != 0;
+    const bool now = k < M && (t & k / R) != 0;
+    const uint64_t m = before != now ? ~0ull : 0ull;
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] ^= m;
+    int j = k >> 1;
+    for (; j >= 32 * R; j >>= 1) {                // between warps: shared-memory rows
+      const int d = j / R;
+      const bool keep_min = (t & d) == 0;
+      swz_store_row<R>(s_x, t, x);
+      __syncthreads();
+      uint64_t p[R];
+      swz_load_row<R>(s_x, t ^ d, p);
+#pragma unroll
+      for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
+      __syncthreads();
+    }
+    if (j == 16 * R) {                            // entry bit 8: the other half warp
+      lane_stage(16);
+      j >>= 1;
+    }
+    if (j == R) {                                 // entry bit 4 alone: a shuffle
+      lane_stage(1);
+    } else if (j > R) {                           // entry bits 4 .. log2(j): transposed
+      halfwarp_transpose16(x, lane, wb);
+      transposed_stages16(x, 31 - __clz(j / R) + 1);
+      halfwarp_transpose16(x, lane, wb);
+    }
+    net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
+  }
+}
+
 }  // namespace bqs

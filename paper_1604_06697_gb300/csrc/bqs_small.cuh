@@ -117,6 +117,7 @@ __device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, in
   // Exchanges between warps (T > 32) store a thread's own row before a barrier and
   // read another's after it, so the staging array doubles as their scratch.
   if constexpr (sizeof(U) == 4 && R == 32) net_sort_transposed<T>(x, t, sw);
+  else if constexpr (sizeof(U) == 8 && R == 16) net_sort_transposed64<T>(x, t, sw);
   else net_sort_looped<R, T>(x, t, sw);
   swz_store_row<R>(sw, t, x);
   sync();
