@@ -446,7 +446,8 @@ def run_pairs(a):
     sk = torch.from_numpy(keys).cuda()
     sv = torch.from_numpy(vals.view(np.int32)).cuda()
     bqs.set_option("pivot", 1)
-    bqs.set_option("local_cutoff", -1)
+    from paper_1604_06697_gb300 import autotune
+    tuned = autotune.tune("int64", n, kind="pairs")["config"]
     wk, wv = torch.empty_like(sk), torch.empty_like(sv)
     for _ in range(a.warmup):
         wk.copy_(sk); wv.copy_(sv); bqs.sort_pairs(wk, wv)
@@ -472,7 +473,7 @@ def run_pairs(a):
         "unit": "pairs/s", "ms_per_step": ms / a.steps, "steps": a.steps, "warmup": a.warmup,
         "dtype": "int64+u32", "data": "synthetic",
         "config": {"workload": "bqs_sort_pairs 2^26 int64 keys mod 2^20, payload = index, seed 1",
-                   "pivot": "sqrt", "local_cutoff": -1},
+                   "pivot": "sqrt", "autotuned": tuned},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak if ach else None, "kernel": "k_partition_tma (pairs)"},
         "gpu_launches": launches, "ordered_check": ok}), flush=True)
@@ -595,7 +596,6 @@ def run_serving(a):
     from paper_1604_06697_gb300 import serving
 
     bqs.set_option("pivot", 1)
-    bqs.set_option("local_cutoff", -1)
     pool = serving.KeyPool(max_size=1 << 26, seed=3)
     rows = []
     for rate in (1000, 2000, 5000, 10000, 20000):

@@ -77,9 +77,10 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
          cache_path: str | None = None, force: bool = False, candidates=None) -> dict:
     """Returns (and caches) the fastest configuration for this workload class.
 
-    kind: "sort" (one array of n keys, uniform values) or "batched" (nseg arrays with
-    log-uniform lengths in [16, 65536] totalling about n keys, sorted by
-    bqs_sort_batched).
+    kind: "sort" (one array of n keys, uniform values), "pairs" (n key-value pairs:
+    keys uniform in [0, 2^20), payload = index, sorted by bqs_sort_pairs) or
+    "batched" (nseg arrays with log-uniform lengths in [16, 65536] totalling about n
+    keys, sorted by bqs_sort_batched).
     """
     import torch
 
@@ -92,7 +93,20 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
         apply(table[key]["config"])
         return table[key]
 
-    if kind == "batched":
+    if kind == "pairs":
+        import numpy as np
+        pk, pv = inputs.make_pairs(n, seed=1)
+        src_k = torch.from_numpy(pk.astype(dtype)).cuda()
+        src_v = torch.from_numpy(pv.view(np.int32)).cuda()
+        work_k, work_v = torch.empty_like(src_k), torch.empty_like(src_v)
+
+        def run():
+            bqs.sort_pairs(work_k, work_v)
+
+        def prep():
+            work_k.copy_(src_k)
+            work_v.copy_(src_v)
+    elif kind == "batched":
         keys, off = inputs.make_segments(nseg, seed=2, dtype=dtype)
         src = torch.from_numpy(keys).cuda()
         toff = torch.from_numpy(off).cuda()
@@ -115,9 +129,10 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
+    sorts = (1,) if kind == "pairs" else SMALL_SORTS   # key-value sorts use one network shape
     cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w)
                            for t, s, l, w in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
-                                                               SMALL_SORTS)]
+                                                               sorts)]
     try:
         for cfg in cands:
             apply(cfg)

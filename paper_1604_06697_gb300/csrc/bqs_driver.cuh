@@ -147,16 +147,16 @@ const std::vector<Variant>& variants() {
   return v;
 }
 
-// Shape of the single-block local sort: keys per block (L) and threads; both ping-pong
-// buffers of L keys (+ payloads) fit in shared memory.
+// Shape of the single-block local partitioning: keys per block (L) and threads; both
+// ping-pong buffers of L keys (+ payloads) fit in shared memory.
 template <class KT, bool PAIRS>
 struct LocalCap {
-  static constexpr int L = PAIRS ? 8192 : (int)(65536 / sizeof(typename KT::U));
-  static constexpr int T = 512;
+  static constexpr int L = PAIRS ? 4096 : (int)(32768 / sizeof(typename KT::U));
+  static constexpr int T = 256;
   static constexpr size_t smem = LocalShape<KT, PAIRS, L>::smem;
   static const void* fn() {
     static const void* f = [] {
-      const void* k = (const void*)k_local_sort<KT, PAIRS, L, T>;
+      const void* k = (const void*)k_local_partition<KT, PAIRS, L, T>;
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       return k;
     }();
@@ -165,7 +165,7 @@ struct LocalCap {
   static int grid();
   static void launch(const Params& P, int p, int grid, cudaStream_t st) {
     fn();
-    k_local_sort<KT, PAIRS, L, T><<<grid, T, smem, st>>>(P, p);
+    k_local_partition<KT, PAIRS, L, T><<<grid, T, smem, st>>>(P, p);
   }
 };
 
@@ -421,13 +421,16 @@ int run_call(const Call& c, Stats& st) {
   const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
   const int tile = var.threads * var.kpt;
   const int small_cutoff = c.partition_only ? 1 : (int)c.opt.small_cutoff;
-  // Segments up to local_cutoff keys are finished by one thread block in shared memory.
+  // Segments up to local_cutoff keys are partitioned down to the small-segment cutoff by
+  // one thread block in shared memory (not below a cutoff of kWarpSortMax keys: the
+  // block's sub-segment lists are sized for that).
   constexpr int kLocalL = LocalCap<KT, PAIRS>::L;
   const int local_cutoff =
-      c.partition_only ? 1
-                       : std::max(small_cutoff, c.opt.local_cutoff < 0
-                                                    ? kLocalL
-                                                    : (int)std::min<int64_t>(c.opt.local_cutoff, kLocalL));
+      (c.partition_only || small_cutoff < kWarpSortMax)
+          ? small_cutoff
+          : std::max(small_cutoff, c.opt.local_cutoff < 0
+                                       ? kLocalL
+                                       : (int)std::min<int64_t>(c.opt.local_cutoff, kLocalL));
 
   const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only);
   Scratch scratch;
@@ -596,19 +599,26 @@ int run_call(const Call& c, Stats& st) {
       P.test_stall = 0;
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
-      if (counts_ev) {
-        // The next level's counts are final once the bookkeeping has run: read them
-        // back now, while this level's fills and sorting networks still run, so the
-        // host enqueues the next level before the stream drains.
-        BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        BQS_CK(cudaEventRecord(counts_ev, s));
-      }
-      k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
-      st.kernel_launches += 3;
+      st.kernel_launches += 2;
+    } else if (cur.local) {
+      // No partition kernel clears the next level's counts this time.
+      BQS_CK(cudaMemsetAsync(&P.ctrl->lists[P.p ^ 1], 0, sizeof(ListCounts), s));
     }
-    if (cur.local) {
+    if (cur.local) {   // its finished sub-segments join the next level's network lists
       st.local_segments += cur.local;
       LocalCap<KT, PAIRS>::launch(P, P.p, (int)std::min<uint32_t>(cur.local, (uint32_t)local_grid), s);
+      st.kernel_launches += 1;
+    }
+    const bool more = nlarge || cur.local;
+    if (more && counts_ev) {
+      // The next level's counts are final once bookkeeping and local partitioning have
+      // run: read them back now, while this level's fills and sorting networks still
+      // run, so the host enqueues the next level before the stream drains.
+      BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      BQS_CK(cudaEventRecord(counts_ev, s));
+    }
+    if (nlarge) {
+      k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
     if (cur.tiny) {
@@ -621,7 +631,7 @@ int run_call(const Call& c, Stats& st) {
       st.kernel_launches += launch_small<KT, PAIRS>(P, P.p, cur.small, cur.group, false, s);
     }
     BQS_CK(cudaGetLastError());
-    if (!nlarge) break;
+    if (!more) break;
     if (counts_ev) {
       BQS_CK(cudaEventSynchronize(counts_ev));
     } else {

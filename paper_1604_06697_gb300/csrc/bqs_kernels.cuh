@@ -118,7 +118,7 @@ __device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity
 // segment is queued on `todo` for k_pivot.
 template <class KT, bool PAIRS>
 __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int64_t len,
-                           int parity, int depth) {
+                           int parity, int depth, bool count_keys = true) {
   Ctrl* c = P.ctrl;
   const int lane = threadIdx.x & 31;
   const unsigned below = lanemask_lt();
@@ -143,14 +143,14 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
     unsigned int base = 0;
     if (lane == leader) {
       base = atomicAdd(counter, (unsigned)__popc(m));
-      atomicAdd(kind == 2 ? &c->local_keys : &c->small_keys, (unsigned long long)keys);
+      if (count_keys) atomicAdd(kind == 2 ? &c->local_keys : &c->small_keys, (unsigned long long)keys);
     }
     base = __shfl_sync(~0u, base, leader);
     if (mine) {
       const unsigned int slot = base + __popc(m & below);
       if (slot < P.l.cap_run) {
         Run r;
-        r.off = off; r.len = len; r.parity = parity; r.pad = 0;
+        r.off = off; r.len = len; r.parity = parity; r.pad = depth;   // depth: local runs
         list[slot] = r;
       } else {
         atomicExch(&c->status, kStatusOverflow);

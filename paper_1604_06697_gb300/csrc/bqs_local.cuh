@@ -1,29 +1,32 @@
-// Single-block local sort: the bottom levels of the recursion inside shared memory.
+// Single-block local partitioning: the bottom partition levels of the recursion inside
+// shared memory.
 //
-// One thread block takes a whole segment of at most L keys, loads it once into a
-// shared-memory buffer, and keeps applying the block partition step of Sec. 3 to all
-// of its unfinished sub-segments at once, ping-ponging between two shared-memory
-// buffers, until every sub-segment has at most kLocalLeaf keys.  Those leaves are
-// finished by the warp sorting network of bqs_small.cuh (the stand-in for the paper's
-// Insertionsort), and the assembled segment is written to HBM once.  The result is the
-// same Quicksort recursion as the global levels (median pivots, three-way split, pivot
-// class excluded from both sides), with one HBM read and one write per key instead of
-// one per level.
+// One thread block takes a whole segment of at most L keys (the `local` list), loads it
+// once into a shared-memory buffer and keeps applying the block partition step of
+// Sec. 3 to all of its unfinished sub-segments at once, ping-ponging between two
+// shared-memory buffers, until every sub-segment is short enough for a sorting network
+// (at most the small-segment cutoff).  After each level the pivot classes are written
+// to the final buffer (the pivot value, as everywhere), and the finished sub-segments
+// are written back to the segment's range in HBM and appended to the next level's
+// network lists.  The recursion is the same as on the global levels (the same pivot
+// rules, three-way split, pivot class excluded from both sides); only the levels
+// between L keys and the cutoff cost one HBM read and one write per key in total
+// instead of one of each per level.
 #pragma once
 
 #include "bqs_small.cuh"
 
 namespace bqs {
 
-constexpr int kLocalMaxAct = 128;  // unfinished sub-segments per level (> L / kLocalLeaf)
-constexpr int kLocalChunk = 256;   // keys per warp work item (32 lanes x 8)
-constexpr int kLocalLeaf = 256;    // sub-segments up to this length go to a warp network
+constexpr int kLocalMaxAct = 64;    // active sub-segments per level (> L / kWarpSortMax)
+constexpr int kLocalMaxLeaf = 128;  // finished sub-segments per level (2 per active one)
+constexpr int kLocalChunk = 256;    // keys per warp work item (32 lanes x 8)
 
 struct SubSeg {
   int begin;   // offset in the block's segment
   int len;
   int buf;     // shared-memory buffer holding its keys
-  int depth;   // local partition levels above it
+  int depth;   // partition levels above it
 };
 
 template <class KT, bool PAIRS, int L>
@@ -34,61 +37,42 @@ struct LocalShape {
   static constexpr size_t smem = 2 * (kbuf + vbuf);
 };
 
-// Sorts len <= 32*R entries at src[0, len) (shared memory, raw keys) into dst[0, len)
-// with one warp; src and dst may be the same.
-template <class KT, bool PAIRS, int R>
-__device__ __forceinline__ void warp_sort_smem(const typename KT::U* src, const uint32_t* vsrc,
-                                               typename KT::U* dst, uint32_t* vdst, int len,
-                                               int lane) {
-  using U = typename KT::U;
-  U x[R];
-  uint32_t y[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int e = lane * R + i;
-    x[i] = e < len ? KT::ord(src[e]) : ~U(0);
-    y[i] = PAIRS ? (e < len ? vsrc[e] : 0xFFFFFFFFu) : 0u;
-  }
-  __syncwarp();
-  net_sort<PAIRS, R, 32>(x, y, lane, (U*)nullptr, (uint32_t*)nullptr);
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int e = lane * R + i;
-    if (e < len) {
-      dst[e] = KT::unord(x[i]);
-      if constexpr (PAIRS) vdst[e] = y[i];
-    }
-  }
-  __syncwarp();
-}
-
+// Pivot of the sub-segment keys[0, len) in shared memory, by the rules route_warp applies
+// to global segments of the same length (inline_pivot): median-of-3 of (first, middle,
+// last), or for the sqrt(n) rule from 64 keys on the median-of-5-medians-of-5 of 25
+// spaced keys; sub-segments here are shorter than the 20000 keys from which the global
+// rule takes a sqrt(n) sample.
 template <class KT, bool PAIRS>
-__device__ __forceinline__ void warp_sort_leaf(const typename KT::U* src, const uint32_t* vsrc,
-                                               typename KT::U* dst, uint32_t* vdst, int len,
-                                               int lane) {
-  if (len <= 32) warp_sort_smem<KT, PAIRS, 1>(src, vsrc, dst, vdst, len, lane);
-  else if (len <= 64) warp_sort_smem<KT, PAIRS, 2>(src, vsrc, dst, vdst, len, lane);
-  else if (len <= 128) warp_sort_smem<KT, PAIRS, 4>(src, vsrc, dst, vdst, len, lane);
-  else warp_sort_smem<KT, PAIRS, 8>(src, vsrc, dst, vdst, len, lane);
-}
-
-// Leaves are recorded as begin | (len - 1) << 15 | buffer << 24 (begin < 2^15, len <= 256).
-__device__ __forceinline__ uint32_t pack_leaf(int begin, int len, int buf) {
-  return (uint32_t)begin | ((uint32_t)(len - 1) << 15) | ((uint32_t)buf << 24);
+__device__ Elem<KT, PAIRS> local_pivot(const Params& P, const typename KT::U* keys,
+                                       const uint32_t* vals, int len) {
+  using E = Elem<KT, PAIRS>;
+  if (P.pivot_rule == 0 || len < 64)
+    return median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, 0),
+                              load_elem<KT, PAIRS>(keys, vals, len / 2),
+                              load_elem<KT, PAIRS>(keys, vals, len - 1));
+  E m[5];
+  for (int g = 0; g < 5; ++g) {
+    E e[5];
+    for (int j = 0; j < 5; ++j)
+      e[j] = load_elem<KT, PAIRS>(keys, vals, ((2 * (5 * g + j) + 1) * (int64_t)len) / 50);
+    m[g] = median5<KT, PAIRS>(e);
+  }
+  return median5<KT, PAIRS>(m);
 }
 
 template <class KT, bool PAIRS, int L, int T>
-__global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
+__global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
   using U = typename KT::U;
-  p = level_parity(P, p);
   using S = LocalShape<KT, PAIRS, L>;
   using E = Elem<KT, PAIRS>;
   constexpr int WARPS = T / 32;
   constexpr int KPL = kLocalChunk / 32;
-  constexpr int MAXLEAF = 2048;
-  static_assert(L / (kLocalLeaf + 1) + 1 <= kLocalMaxAct, "active list capacity");
-  static_assert(L <= 32768 && kLocalLeaf <= 256, "leaf record packing");
+  static_assert(L / (kWarpSortMax + 1) + 1 <= kLocalMaxAct, "active list capacity");
+  static_assert(2 * kLocalMaxAct <= kLocalMaxLeaf, "leaf list capacity");
+  static_assert(L < 65536, "packed per-sub-segment counts");
 
+  p = level_parity(P, p);
+  const int q = p ^ 1;
   extern __shared__ __align__(16) unsigned char smem[];
   // buffer b: keys at smem + b*kbuf, payloads at smem + 2*kbuf + b*vbuf
   auto kb = [&](int b) { return reinterpret_cast<U*>(smem + (size_t)b * S::kbuf); };
@@ -98,75 +82,49 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
   __shared__ uint32_t s_pv[kLocalMaxAct];
   __shared__ uint32_t s_vstart[kLocalMaxAct + 1];  // work-item starts, padded to kLocalChunk
   __shared__ uint32_t s_cnt[kLocalMaxAct];    // (#<) | (#>) << 16 claimed so far
-  __shared__ uint32_t s_leaf[MAXLEAF];
+  __shared__ SubSeg s_leaf[kLocalMaxLeaf];    // finished this level
+  __shared__ int s_fill[kLocalMaxAct][2];     // pivot class: begin, length
   __shared__ int s_nact[2], s_nleaf;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned int count = min(P.ctrl->lists[p].local, P.l.cap_run);
-  const int depth_cap = 2 * (31 - __clz(L)) + 8;   // local Introsort-style limit
-
-  // Sorts every recorded leaf into buffer 0, warps taking leaves round-robin.
-  auto flush_leaves = [&]() {
-    const int nl = s_nleaf;
-    for (int f = warp; f < nl; f += WARPS) {
-      const uint32_t q = s_leaf[f];
-      const int b = (int)(q & 0x7FFF), ln = (int)((q >> 15) & 0x1FF) + 1, bf = (int)(q >> 24);
-      warp_sort_leaf<KT, PAIRS>(kb(bf) + b, vb(bf) + b, kb(0) + b, vb(0) + b, ln, lane);
-    }
-  };
+  U* fk = (U*)P.b.final_key;
+  uint32_t* fv = P.b.final_val;
 
   for (unsigned int r = blockIdx.x; r < count; r += gridDim.x) {
     const Run run = P.l.local[p][r];
     const int len = (int)run.len;
+    const int X = run.parity;                  // leaves go back to the run's own range
+    U* gk = (U*)P.b.key[X] + run.off;
+    uint32_t* gv = PAIRS ? P.b.val[X] + run.off : nullptr;
     {
-      const U* g = (const U*)P.b.key[run.parity] + run.off;
-      const uint32_t* gv = PAIRS ? P.b.val[run.parity] + run.off : nullptr;
       U* k0 = kb(0);
       uint32_t* v0 = vb(0);
       for (int i = tid; i < len; i += T) {
-        k0[i] = g[i];
+        k0[i] = gk[i];
         if constexpr (PAIRS) v0[i] = gv[i];
       }
     }
     if (tid == 0) {
-      s_nleaf = 0;
+      s_nact[0] = 1;
       s_nact[1] = 0;
-      if (len <= kLocalLeaf) {
-        s_nact[0] = 0;
-        s_leaf[0] = pack_leaf(0, len, 0);
-        s_nleaf = 1;
-      } else {
-        s_nact[0] = 1;
-        s_act[0][0] = SubSeg{0, len, 0, 0};
-      }
+      s_act[0][0] = SubSeg{0, len, 0, run.pad};
     }
     __syncthreads();
 
     for (int cur = 0;; cur ^= 1) {
       const int nact = s_nact[cur];
       if (nact == 0) break;
-      // Keep room for this level's leaves (at most two per active sub-segment).
-      if (s_nleaf + 2 * nact > MAXLEAF) {
-        flush_leaves();
-        __syncthreads();
-        if (tid == 0) s_nleaf = 0;
-      }
 
-      // Pivots (median of three medians of three of nine spaced keys; the midpoint of
-      // the ord-key range past the local depth cap) and work-item starts.
+      // Pivots (the depth-limit fallback: midpoint of the ord-key range, then of the
+      // payload range, as in k_pivot) and work-item starts.
       if (tid < nact) {
         const SubSeg a = s_act[cur][tid];
         const U* kk = kb(a.buf) + a.begin;
         const uint32_t* vv = vb(a.buf) + a.begin;
         E piv;
-        if (a.depth < depth_cap) {
-          E m[3];
-          for (int g = 0; g < 3; ++g)
-            m[g] = median3<KT, PAIRS>(
-                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 0) + 1) * a.len) / 18),
-                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 1) + 1) * a.len) / 18),
-                load_elem<KT, PAIRS>(kk, vv, ((2 * (3 * g + 2) + 1) * a.len) / 18));
-          piv = median3<KT, PAIRS>(m[0], m[1], m[2]);
+        if (a.depth < P.depth_limit) {
+          piv = local_pivot<KT, PAIRS>(P, kk, vv, a.len);
         } else {
           U kmin = ~U(0), kmax = 0;
           for (int i = 0; i < a.len; ++i) {
@@ -184,6 +142,7 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
             }
             piv.v = vmin + (vmax - vmin) / 2;
           }
+          atomicAdd(&P.ctrl->fallbacks, 1ull);
         }
         s_pk[tid] = KT::unord(piv.k);
         s_pv[tid] = piv.v;
@@ -209,11 +168,13 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
           if (j <= nact) s_vstart[j] = run_;
           run_ += v[i];
         }
-        if (lane == 0) s_nact[cur ^ 1] = 0;
+        if (lane == 0) { s_nact[cur ^ 1] = 0; s_nleaf = 0; }
       }
       __syncthreads();
 
-      // Partition pass over all active sub-segments: one warp per 256-key work item.
+      // Partition pass over all active sub-segments (Algorithm 3 per 256-key work
+      // item): one warp per item, outcomes counted per lane, one shared-memory atomic
+      // per item reserves both runs.
       const int nitems = (int)(s_vstart[nact] / kLocalChunk);
       for (int it = warp; it < nitems; it += WARPS) {
         const uint32_t v0 = (uint32_t)it * kLocalChunk;
@@ -279,45 +240,59 @@ __global__ void __launch_bounds__(T) k_local_sort(Params P, int p) {
       }
       __syncthreads();
 
-      // Children of every active sub-segment; the pivot class is final: it is written
-      // to buffer 0 right away (usually a single key).
+      // Children: sub-segments above the small-segment cutoff stay active, the others
+      // are finished here; the pivot class is final.
       if (tid < nact) {
         const SubSeg a = s_act[cur][tid];
         const int nlt = (int)(s_cnt[tid] & 0xFFFF), ngt = (int)(s_cnt[tid] >> 16);
-        const int neq = a.len - nlt - ngt;
-        U* k0 = kb(0) + a.begin + nlt;
-        uint32_t* v0 = vb(0) + a.begin + nlt;
-        for (int i = 0; i < neq; ++i) {
-          k0[i] = s_pk[tid];
-          if constexpr (PAIRS) v0[i] = s_pv[tid];
-        }
+        s_fill[tid][0] = a.begin + nlt;
+        s_fill[tid][1] = a.len - nlt - ngt;
         const SubSeg kids[2] = {SubSeg{a.begin, nlt, a.buf ^ 1, a.depth + 1},
                                 SubSeg{a.begin + a.len - ngt, ngt, a.buf ^ 1, a.depth + 1}};
         for (int c = 0; c < 2; ++c) {
           if (kids[c].len == 0) continue;
-          if (kids[c].len <= kLocalLeaf)
-            s_leaf[atomicAdd(&s_nleaf, 1)] = pack_leaf(kids[c].begin, kids[c].len, kids[c].buf);
+          if (kids[c].len <= P.small_cutoff)
+            s_leaf[atomicAdd(&s_nleaf, 1)] = kids[c];
           else
             s_act[cur ^ 1][atomicAdd(&s_nact[cur ^ 1], 1)] = kids[c];
         }
       }
       __syncthreads();
-    }
-    flush_leaves();
-    __syncthreads();
 
-    // The assembled segment goes to the final buffer once.
-    {
-      U* g = (U*)P.b.final_key + run.off;
-      uint32_t* gv = PAIRS ? P.b.final_val + run.off : nullptr;
-      const U* k0 = kb(0);
-      const uint32_t* v0 = vb(0);
-      for (int i = tid; i < len; i += T) {
-        g[i] = k0[i];
-        if constexpr (PAIRS) gv[i] = v0[i];
+      // Finished keys leave shared memory: pivot classes to the final buffer, finished
+      // sub-segments back to the run's range (one warp per sub-segment, coalesced).
+      const int nleaf = s_nleaf;
+      for (int f = warp; f < nact + nleaf; f += WARPS) {
+        if (f < nact) {
+          const int b = s_fill[f][0], n = s_fill[f][1];
+          const U pk = s_pk[f];
+          const uint32_t pv = s_pv[f];
+          for (int i = lane; i < n; i += 32) {
+            fk[run.off + b + i] = pk;
+            if constexpr (PAIRS) fv[run.off + b + i] = pv;
+          }
+        } else {
+          const SubSeg a = s_leaf[f - nact];
+          const U* ks = kb(a.buf) + a.begin;
+          const uint32_t* vs = vb(a.buf) + a.begin;
+          for (int i = lane; i < a.len; i += 32) {
+            gk[a.begin + i] = ks[i];
+            if constexpr (PAIRS) gv[a.begin + i] = vs[i];
+          }
+        }
       }
+      __syncthreads();   // the leaves' keys are in HBM before anyone routes them
+
+      // Appended to the network lists of the next level (warp-aggregated, like every
+      // child segment); their keys were counted when the run was routed here.
+      for (int base = warp * 32; base < nleaf; base += WARPS * 32) {
+        const int f = base + lane;
+        const bool has = f < nleaf;
+        const SubSeg a = has ? s_leaf[f] : SubSeg{0, 0, 0, 0};
+        route_warp<KT, PAIRS>(P, q, has, run.off + a.begin, a.len, X, a.depth, false);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

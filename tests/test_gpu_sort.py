@@ -83,21 +83,47 @@ def test_small_cutoffs(bqs, cutoff):
             assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
 
 
+@pytest.mark.parametrize("pivot", [0, 1])
 @pytest.mark.parametrize("local", [-1, 0, 3000, 16384])
-@pytest.mark.parametrize("cutoff", [16, 256, 2048])
-def test_local_sort_cutoffs(bqs, cutoff, local):
-    # Segments above the small cutoff and up to the local cutoff are finished by one
-    # block in shared memory; 0 turns that off (every such segment is partitioned).
+@pytest.mark.parametrize("cutoff", [16, 256, 1000, 2048])
+def test_local_partition_cutoffs(bqs, cutoff, local, pivot):
+    # Segments above the small cutoff and up to the local cutoff are partitioned down to
+    # the small cutoff by one block in shared memory (for cutoffs of at least 256 keys);
+    # 0 turns that off (every such segment is partitioned level by level in HBM).
     bqs.set_option("small_cutoff", cutoff)
     bqs.set_option("local_cutoff", local)
+    bqs.set_option("pivot", pivot)
     for dtype in DTYPES:
         for n, dist in [(257, "uniform"), (2049, "reversed"), (16384, "uniform"),
                         (16385, "mod_sqrt"), (300_001, "uniform"), (100_000, "all_equal"),
-                        (200_000, "swapped_1pct")]:
+                        (200_000, "swapped_1pct"), (1 << 20, "uniform")]:
             a = inputs.make_keys(n, dtype, dist, seed=n + cutoff)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
+            st = bqs.stats()
+            assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n, (n, dist, st)
+            if local != 0 and cutoff >= 256 and n == 1 << 20:
+                assert st["local_segments"] > 0
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_local_partition_depth_fallback_and_pairs(bqs, dtype):
+    import torch
+    bqs.set_option("local_cutoff", -1)
+    for limit in (0, 2):
+        bqs.set_option("depth_limit", limit)
+        for dist in ("uniform", "mod_sqrt", "all_equal"):
+            a = inputs.make_keys(300_001, dtype, dist, seed=limit)
             assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
-    if local != 0:
-        assert bqs.stats()["local_segments"] > 0
+    bqs.set_option("depth_limit", -1)
+    n = 1 << 20
+    k = (inputs.splitmix64(21, n) % np.uint64(3000)).astype(dtype)
+    v = np.arange(n, dtype=np.uint32)[np.argsort(inputs.splitmix64(22, n))].astype(np.uint32)
+    tk, tv = torch.from_numpy(k).cuda(), torch.from_numpy(v.view(np.int32)).cuda()
+    bqs.sort_pairs(tk, tv)
+    wk, wv = oracle.sort_pairs(k, v)
+    assert_same_bits(tk.cpu().numpy(), wk)
+    assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
+    assert bqs.stats()["local_segments"] > 0
 
 
 def test_float64_special_values(bqs):
