@@ -178,10 +178,13 @@ typedef enum {
                                segmented sorts; bqs_partition and bqs_sort_noalloc
                                always use 0) */
   BQS_OPT_SMALL_SORT = 9    /* sorting network for segments of 257 .. small-cutoff keys:
-                               0 (default) = one warp per segment up to 1024 keys and
-                               one 64-thread (32-bit keys) or 128-thread (64-bit keys)
-                               block above; 1 = one 256-thread block per segment.
-                               Key-value sorts always use 256-thread blocks. */
+                               0 (default) = key-only: one warp per segment up to 1024
+                               (512 for 64-bit keys) keys and one 64-thread (32-bit) or
+                               128-thread (64-bit) block above; key-value: the pairs
+                               packed into 64-bit keys ((ord(key) - min) << 32 |
+                               payload) where the segment's key range allows (always
+                               for 32-bit keys), one 256-thread block otherwise;
+                               1 = one 256-thread block per segment. */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

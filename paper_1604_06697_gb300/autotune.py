@@ -129,10 +129,9 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
-    sorts = (1,) if kind == "pairs" else SMALL_SORTS   # key-value sorts use one network shape
     cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w)
                            for t, s, l, w in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
-                                                               sorts)]
+                                                               SMALL_SORTS)]
     try:
         for cfg in cands:
             apply(cfg)

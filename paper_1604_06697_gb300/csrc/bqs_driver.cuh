@@ -246,6 +246,12 @@ int launch_small(const Params& P, int p, uint32_t small, uint32_t group, bool de
       if constexpr (!PAIRS) k_small_warps<KT, PAIRS><<<(int)g, 128, 0, s>>>(P, p);
     } else {
       const uint32_t g = device_counts ? 16 * sms : std::min<uint32_t>(small, 16 * sms);
+      if constexpr (PAIRS) {
+        if (P.small_sort == 0) {   // packable segments first; k_small_block takes the rest
+          k_small_pairs_packed<KT><<<(int)g, 128, 0, s>>>(P, p);
+          ++n;
+        }
+      }
       k_small_block<KT, PAIRS><<<(int)g, 256, 0, s>>>(P, p);
     }
     ++n;

@@ -164,17 +164,123 @@ __global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<K
   }
 }
 
+// ---- key-value segments as packed 64-bit keys ------------------------------------------
+//
+// (key, payload) pairs are ordered lexicographically.  When the order images of a
+// segment's keys span less than 2^32 (always for 32-bit keys), the pair maps to
+// ((ord(key) - min) << 32) | payload, a 64-bit integer in the same order, and the
+// segment is sorted by the key-only 64-bit networks; other segments are left to the
+// 256-thread key-value network (k_small_block), which makes the same test.
+
+// Smallest ord image of segment r's keys and whether the pairs pack (block-wide; every
+// thread of the block must call it; s_red holds 2 * (blockDim.x / 32) entries).
+template <class KT>
+__device__ __forceinline__ bool pairs_pack(const Params& P, const Run& r, typename KT::U& kmin,
+                                           typename KT::U* s_red) {
+  using U = typename KT::U;
+  if constexpr (sizeof(U) == 4) {
+    kmin = 0;
+    return true;
+  } else {
+    const U* src = (const U*)P.b.key[r.parity] + r.off;
+    U lo = ~U(0), hi = 0;
+    for (int i = threadIdx.x; i < (int)r.len; i += blockDim.x) {
+      const U k = KT::ord(src[i]);
+      lo = k < lo ? k : lo;
+      hi = k > hi ? k : hi;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const U a = (U)__shfl_xor_sync(~0u, (unsigned long long)lo, o);
+      const U b = (U)__shfl_xor_sync(~0u, (unsigned long long)hi, o);
+      lo = a < lo ? a : lo;
+      hi = b > hi ? b : hi;
+    }
+    const int warps = blockDim.x >> 5, w = threadIdx.x >> 5;
+    __syncthreads();                                  // s_red free from earlier use
+    if ((threadIdx.x & 31) == 0) { s_red[w] = lo; s_red[warps + w] = hi; }
+    __syncthreads();
+    lo = s_red[0];
+    hi = s_red[warps];
+    for (int i = 1; i < warps; ++i) {
+      lo = s_red[i] < lo ? s_red[i] : lo;
+      hi = s_red[warps + i] > hi ? s_red[warps + i] : hi;
+    }
+    kmin = lo;
+    return hi - lo <= (U)0xFFFFFFFFull;
+  }
+}
+
+template <class KT, int R, int T>
+__device__ __forceinline__ void packed_pairs_run(const Params& P, const Run& r, typename KT::U kmin,
+                                                 uint64_t* sw) {
+  using U = typename KT::U;
+  using S = RowSwizzle<uint64_t, R>;
+  const int t = threadIdx.x;
+  const U* src = (const U*)P.b.key[r.parity] + r.off;
+  const uint32_t* vsrc = P.b.val[r.parity] + r.off;
+  U* dst = (U*)P.b.final_key + r.off;
+  uint32_t* vdst = P.b.final_val + r.off;
+  const int len = (int)r.len;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = i * T + t;
+    sw[S::pos(e)] = e < len ? ((uint64_t)(KT::ord(src[e]) - kmin) << 32) | vsrc[e] : ~0ull;
+  }
+  __syncthreads();
+  uint64_t x[R];
+  swz_load_row<R>(sw, t, x);
+  if constexpr (R == 16) net_sort_transposed64<T>(x, t, sw);
+  else net_sort_looped<R, T>(x, t, sw);
+  swz_store_row<R>(sw, t, x);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int e = i * T + t;
+    if (e < len) {
+      const uint64_t v = sw[S::pos(e)];
+      dst[e] = KT::unord(kmin + (U)(v >> 32));
+      vdst[e] = (uint32_t)v;
+    }
+  }
+  __syncthreads();
+}
+
+// Key-value segments of the `small` list whose keys pack, one 128-thread block each.
+template <class KT>
+__global__ void __launch_bounds__(128, 4) k_small_pairs_packed(Params P, int p) {
+  using U = typename KT::U;
+  constexpr int T = 128;
+  p = level_parity(P, p);
+  __shared__ __align__(16) uint64_t s_w[kMaxSmall];
+  __shared__ U s_red[2 * (T / 32)];
+  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
+    const Run r = P.l.small[p][s];
+    U kmin;
+    if (!pairs_pack<KT>(P, r, kmin, s_red)) continue;   // k_small_block's
+    if (r.len <= 512) packed_pairs_run<KT, 4, T>(P, r, kmin, s_w);
+    else if (r.len <= 1024) packed_pairs_run<KT, 8, T>(P, r, kmin, s_w);
+    else packed_pairs_run<KT, 16, T>(P, r, kmin, s_w);
+  }
+}
+
 // One 256-thread block per segment of kWarpSortMax+1 .. kMaxSmall keys (list `small`):
-// key-value sorts, and key-only sorts with BQS_OPT_SMALL_SORT = 1.
+// key-value sorts (with small_sort = 0 only the segments whose keys do not pack), and
+// key-only sorts with BQS_OPT_SMALL_SORT = 1.
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_small_block(Params P, int p) {
   using U = typename KT::U;
   p = level_parity(P, p);
   __shared__ __align__(16) U s_x[kMaxSmall];
   __shared__ __align__(16) uint32_t s_y[PAIRS ? kMaxSmall : 1];
+  __shared__ U s_red[PAIRS ? 16 : 1];
   const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
     const Run r = P.l.small[p][s];
+    if constexpr (PAIRS) {
+      U kmin;
+      if (P.small_sort == 0 && pairs_pack<KT>(P, r, kmin, s_red)) continue;   // packed
+    }
     if (r.len <= 512) sort_run<KT, PAIRS, 2, 256>(P, r, threadIdx.x, s_x, s_y, true);
     else if (r.len <= 1024) sort_run<KT, PAIRS, 4, 256>(P, r, threadIdx.x, s_x, s_y, true);
     else sort_run<KT, PAIRS, 8, 256>(P, r, threadIdx.x, s_x, s_y, true);

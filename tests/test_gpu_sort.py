@@ -304,3 +304,33 @@ def test_statistics_of_a_sort_without_partition_levels(bqs):
         st = bqs.stats()
         assert st["levels"] == 0 and st["moved_keys"] == 0 and st["equal_keys"] == 0
         assert st["small_keys"] == n and st["local_keys"] == 0
+
+
+def _pairs_case(dtype, n, kind, seed):
+    r = inputs.splitmix64(seed, n)
+    if kind == "dense":          # key range far below 2^32: every segment packs
+        k = (r % np.uint64(5000)).astype(dtype)
+    elif kind == "wide":         # full range: 64-bit segments do not pack
+        k = r.view(np.int64).astype(dtype) if dtype != "float64" else \
+            (r >> np.uint64(11)).astype(np.float64) * 2.0 ** -20 - 2.0 ** 32
+    else:                        # half dense cluster, half wide: both paths in one sort
+        k = np.where(r & np.uint64(1), r % np.uint64(1000), r >> np.uint64(1)).astype(np.int64)
+        k = k.astype(dtype)
+    v = np.arange(n, dtype=np.uint32)[np.argsort(inputs.splitmix64(seed + 1, n))].astype(np.uint32)
+    return np.ascontiguousarray(k), v
+
+
+@pytest.mark.parametrize("small_sort", [0, 1])
+@pytest.mark.parametrize("kind", ["dense", "wide", "mixed"])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_pairs_packed_and_fallback_networks(bqs, dtype, kind, small_sort):
+    import torch
+    bqs.set_option("small_sort", small_sort)
+    for cutoff, n in ((300, 200_003), (1024, 1 << 20), (2048, 777_777)):
+        bqs.set_option("small_cutoff", cutoff)
+        keys, vals = _pairs_case(dtype, n, kind, seed=cutoff)
+        tk, tv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+        bqs.sort_pairs(tk, tv)
+        wk, wv = oracle.sort_pairs(keys, vals)
+        assert_same_bits(tk.cpu().numpy(), wk)
+        assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
