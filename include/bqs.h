@@ -162,8 +162,11 @@ typedef enum {
   BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
   BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */
   BQS_OPT_TILE = 4,         /* partition tile variant: 0 = default, 1..N autotuner choices */
-  BQS_OPT_LOCAL_CUTOFF = 5, /* segments up to this size are sorted inside one thread block
-                               (-1 = as large as one block holds; 0 = off, the default) */
+  BQS_OPT_LOCAL_CUTOFF = 5, /* segments up to this size are partitioned down to the small
+                               cutoff inside one thread block's shared memory (one HBM
+                               read and write for those levels); -1 = as large as one
+                               block holds (8192 keys for 32-bit keys, 4096 otherwise);
+                               0 = off, the default; ignored below a small cutoff of 256 */
   BQS_OPT_WAIT_LIMIT = 6,   /* polls before a bounded device-side wait gives up and the
                                call returns BQS_ERR_TIMEOUT (default 2^26, seconds) */
   BQS_OPT_TEST_STALL = 7,   /* failure-path testing: 1 makes the first partition launch

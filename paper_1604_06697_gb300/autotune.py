@@ -3,7 +3,7 @@
 Chooses, for one workload class (dtype, size bucket, single array or batch), the
 partition tile variant (threads x keys per thread), the small-segment cutoff, the
 small-segment network shape (one warp / warp group per segment, or one 256-thread
-block) and the single-block local-sort cutoff by timing every candidate on a synthetic input
+block) and the single-block local-partitioning cutoff by timing every candidate on a synthetic input
 of that class with CUDA events.  Results are cached in a JSON file keyed by GPU
 name, dtype, workload kind and log2 size bucket, so a later process applies the
 choice without re-timing.  The tuner only sets the library's options; every

@@ -112,7 +112,7 @@ struct Ctrl {
   int more[8];                      // per level (mod 8): another level has work
   unsigned long long levels_run;    // levels that partitioned something
   unsigned long long active_total;  // sum of partitioned keys over those levels
-  unsigned long long local_runs;    // segments finished by the single-block sort
+  unsigned long long local_runs;    // segments partitioned by one block in shared memory
   unsigned long long small_runs;    // segments finished by the sorting networks
 };
 

@@ -663,7 +663,7 @@ int run_call(const Call& c, Stats& st) {
     st.local_keys = (int64_t)host->local_keys;
     st.fallback_pivots = (int64_t)host->fallbacks;
   } else if (!c.partition_only) {
-    // A single array that went straight to a network or the single-block sort:
+    // A single array that went straight to a network or the single-block partitioning:
     // nothing was read back, and the counts follow from where it was routed.
     st.small_keys = (cur.tiny | cur.small | cur.group) ? c.n : 0;
     st.local_keys = cur.local ? c.n : 0;

@@ -1,5 +1,5 @@
 // The level loop on the device: a CUDA-graph conditional `while` node whose body is one
-// level (pivot, partition, bookkeeping, fills, small-segment and local sorts).  Used
+// level (pivot, partition, bookkeeping, fills, local partitioning, networks).  Used
 // when a sort is enqueued on a stream that is being captured into a CUDA graph: the
 // host then reads nothing back, every kernel takes its level parity from the control
 // block, and the last kernel of the body decides whether another level follows.

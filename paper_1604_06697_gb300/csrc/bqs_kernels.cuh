@@ -111,8 +111,8 @@ __device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity
 
 // Warp-cooperative append of one child segment per lane (`active` lanes with len > 0)
 // to the lists of level q: the sorting network (len <= small_cutoff), the single-block
-// sort (len <= local_cutoff) or another partition level.  Every lane of the warp must
-// call it.  Slots come from one atomic per warp and list; a large segment's slot and
+// partitioning (len <= local_cutoff) or another partition level.  Every lane of the warp
+// must call it.  Slots come from one atomic per warp and list; a large segment's slot and
 // first tile come from one packed 64-bit atomic, so tile0 grows with the slot index.
 // A large segment's pivot is chosen here when one thread can do it; otherwise the
 // segment is queued on `todo` for k_pivot.

@@ -8,8 +8,7 @@
 //   * exchanges between threads of one warp use __shfl_xor_sync (or, for 32-bit keys
 //     with R = 32, register compare-exchanges after a transpose of the warp's block),
 //   * only exchanges between warps go through shared memory.
-// Used by the small-segment sorts (bqs_small.cuh), the single-block local sort and the
-// pivot-sample sort.
+// Used by the small-segment sorts (bqs_small.cuh) and the pivot-sample sort.
 #pragma once
 
 #include "bqs_common.cuh"
