@@ -75,26 +75,38 @@ __device__ __forceinline__ void load_row(const U* src, U (&x)[R]) {
 
 constexpr int ilog2_c(int v) { return v <= 1 ? 0 : 1 + ilog2_c(v >> 1); }
 
-// Staging layout for rows of R entries (row t = the entries thread t holds).  Entry e
-// of row e / R lives at pos(e): its 16-byte chunk index within the row is XORed with
-// key(row).  Then 16-byte row accesses by 8 consecutive threads (one shared-memory
-// wavefront) touch 8 different bank groups, and striped accesses (entry i*T + t by
-// thread t: coalesced with global memory) by a warp, or a half warp for 8-byte keys,
-// XOR their chunk index with one constant, which keeps their banks distinct.  Rows
-// shorter than one chunk are left unswizzled.
+// Staging layout for rows of R entries (row t = the entries thread t holds).
+//  * Rows of 16 eight-byte entries (128 bytes) are padded by 16 bytes: row r starts at
+//    entry r * (R + 2).  16-byte accesses to one chunk of 8 consecutive rows then touch
+//    8 different bank groups, a whole row read by consecutive threads (the transposes)
+//    is contiguous, and the address of entry (r, c) is plain arithmetic.  (For rows of
+//    32 four-byte entries the XOR form below measured slightly faster.)
+//  * Other rows are XOR-swizzled: entry e of row e / R lives at pos(e), its 16-byte
+//    chunk index within the row XORed with key(row), with the same two properties for
+//    16-byte row accesses and striped accesses (entry i*T + t by thread t) by a warp, or
+//    a half warp for 8-byte keys.  Rows shorter than one chunk are left as they are.
 template <class U, int R>
 struct RowSwizzle {
   static constexpr int EPC = 16 / (int)sizeof(U);        // entries per 16-byte chunk
   static constexpr bool kChunked = R >= EPC;
   static constexpr int C = kChunked ? R / EPC : 1;        // chunks per row
   static constexpr int LOGC = ilog2_c(C);
+  static constexpr bool kPadded = sizeof(U) == 8 && R * (int)sizeof(U) == 128;
+  static constexpr int STRIDE = kPadded ? R + EPC : R;    // entries between row starts
   __device__ static __forceinline__ int key(int row) {
-    if constexpr (!kChunked) return 0;
+    if constexpr (!kChunked || kPadded) return 0;
     else if constexpr (LOGC >= 3) return row & 7;
     else return (row >> (3 - LOGC)) & (C - 1);
   }
-  __device__ static __forceinline__ int pos(int e) { return e ^ (key(e / R) * EPC); }
+  __device__ static __forceinline__ int pos(int e) {
+    if constexpr (kPadded) return e + (e / R) * EPC;
+    else return e ^ (key(e / R) * EPC);
+  }
 };
+
+// Staging entries for T rows of R entries.
+template <class U, int R, int T>
+constexpr int staging_entries() { return T * RowSwizzle<U, R>::STRIDE; }
 
 template <int R, class U>
 __device__ __forceinline__ void swz_store_row(U* base, int row, const U (&x)[R]) {
@@ -106,7 +118,7 @@ __device__ __forceinline__ void swz_store_row(U* base, int row, const U (&x)[R])
       union { uint4 v; U e[S::EPC]; } u;
 #pragma unroll
       for (int w = 0; w < S::EPC; ++w) u.e[w] = x[c * S::EPC + w];
-      reinterpret_cast<uint4*>(base)[row * S::C + (c ^ kq)] = u.v;
+      reinterpret_cast<uint4*>(base)[row * (S::STRIDE / S::EPC) + (c ^ kq)] = u.v;
     }
   } else {
     store_row<R>(base + row * R, x);
@@ -121,7 +133,7 @@ __device__ __forceinline__ void swz_load_row(const U* base, int row, U (&x)[R]) 
 #pragma unroll
     for (int c = 0; c < S::C; ++c) {
       union { uint4 v; U e[S::EPC]; } u;
-      u.v = reinterpret_cast<const uint4*>(base)[row * S::C + (c ^ kq)];
+      u.v = reinterpret_cast<const uint4*>(base)[row * (S::STRIDE / S::EPC) + (c ^ kq)];
 #pragma unroll
       for (int w = 0; w < S::EPC; ++w) x[c * S::EPC + w] = u.e[w];
     }
@@ -308,7 +320,7 @@ __device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
 // conflict-free) instead of one shuffle and three ALU operations per key and stage.
 
 // Transposes a warp's 32 x 32 block: afterwards x[i] of lane l is the entry that was
-// x[l] of lane i.  wb: the warp's 1024-word swizzled staging rows.
+// x[l] of lane i.  wb: the warp's 32 staging rows.
 __device__ __forceinline__ void warp_transpose32(uint32_t (&x)[32], int lane, uint32_t* wb) {
   using S = RowSwizzle<uint32_t, 32>;
   swz_store_row<32>(wb, lane, x);                         // row `lane`, 16-byte chunks
@@ -339,7 +351,7 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
   constexpr int R = 32, M = R * T;
   uint32_t none[R];
   const int lane = t & 31;
-  uint32_t* wb = s_x + (t >> 5) * 1024;
+  uint32_t* wb = s_x + (t >> 5) * 32 * RowSwizzle<uint32_t, 32>::STRIDE;
   net_phases_upto<R, T, 2, uint32_t>(x, none, t);                  // phases 2 .. 32
   for (int k = 2 * R; k <= M; k <<= 1) {
     const bool before = (t & (k >> 1) / R) != 0;
@@ -379,7 +391,7 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
 // half warp transposes its 16 x 16 block (register i of lane l <-> register l of lane
 // i within the half), which brings entry bits 4..7 into the registers; bit 8 (lane
 // bit 4) stays a shuffle with the other half warp, bits above a shared-memory
-// exchange between warps.  Each half warp's block is 2 KB of swizzled staging rows.
+// exchange between warps.  Each half warp's block is 16 padded staging rows.
 
 __device__ __forceinline__ void halfwarp_transpose16(uint64_t (&x)[16], int lane, uint64_t* wb) {
   using S = RowSwizzle<uint64_t, 16>;
@@ -410,7 +422,7 @@ __device__ __forceinline__ void net_sort_transposed64(uint64_t (&x)[16], int t, 
   constexpr int R = 16, M = R * T;
   uint32_t none[R];
   const int lane = t & 31;
-  uint64_t* wb = s_x + (t >> 5) * 512;
+  uint64_t* wb = s_x + (t >> 5) * 32 * RowSwizzle<uint64_t, 16>::STRIDE;
   auto lane_stage = [&](int d) {
     const bool keep_min = (t & d) == 0;
 #pragma unroll

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
   constexpr int kMax = small_warp_max<KT, PAIRS>();
   static_assert(kMax >= 512, "launched only for key-only sorts");
   p = level_parity(P, p);
-  __shared__ __align__(16) U s_x[4][kMax];
+  __shared__ __align__(16) U s_x[4][staging_entries<U, kMax / 32, 32>()];
   const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (unsigned int s = blockIdx.x * 4 + warp; s < count; s += gridDim.x * 4) {
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<K
   using G = SmallGroup<KT>;
   static_assert(!PAIRS, "launched only for key-only sorts");
   p = level_parity(P, p);
-  __shared__ __align__(16) U s_x[kMaxSmall];
+  __shared__ __align__(16) U s_x[staging_entries<U, G::RMAX, G::T>()];
   const unsigned int count = min(P.ctrl->lists[p].group, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
     const Run r = P.l.group[p][s];
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128, 4) k_small_pairs_packed(Params P, int p) 
   using U = typename KT::U;
   constexpr int T = 128;
   p = level_parity(P, p);
-  __shared__ __align__(16) uint64_t s_w[kMaxSmall];
+  __shared__ __align__(16) uint64_t s_w[staging_entries<uint64_t, kMaxSmall / T, T>()];
   __shared__ U s_red[2 * (T / 32)];
   const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
