@@ -49,8 +49,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="sort",
-                    choices=["sort", "pairs", "batched", "serving", "matrix"],
-                    help="sort (the default headline line), pairs, batched, serving or matrix")
+                    choices=["sort", "pairs", "batched", "serving", "matrix", "pivots"],
+                    help="sort (the default headline line), pairs, batched, serving, matrix or "
+                         "pivots")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and use --tile/--small/--local instead")
@@ -622,6 +623,53 @@ def run_matrix(a):
                       "data": "synthetic", "rows": rows}), flush=True)
 
 
+PIVOT_RULES = ["median-of-3", "median-of-sqrt(n)", "median-of-5", "median-of-23",
+               "median-of-3-medians-of-3", "median-of-3-medians-of-5", "median-of-5-medians-of-5"]
+
+
+def run_pivots(a):
+    """The pivot rules of Sec. 4 on the same input: levels and keys/s per rule."""
+    import torch
+
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import autotune, inputs
+
+    n = 1 << a.log2n
+    bqs.set_option("pivot", 1)
+    tuned = autotune.tune(a.dtype, n, kind="sort")["config"]
+    src = torch.from_numpy(inputs.make_keys(n, a.dtype, a.dist, a.seed)).cuda()
+    work = torch.empty_like(src)
+    peak, _ = measured_peak_gbs()
+    rows = []
+    for rule, name in enumerate(PIVOT_RULES):
+        bqs.set_option("pivot", rule)
+        for _ in range(a.warmup):
+            work.copy_(src)
+            bqs.sort(work)
+        bqs.set_option("timing", 1)
+        best, pm, pb, lv = float("inf"), 0.0, 0.0, 0
+        for _ in range(a.steps):
+            work.copy_(src)
+            ms = _cuda_ms(lambda: bqs.sort(work))
+            st = bqs.stats()
+            if ms < best:
+                best, pm, pb, lv = ms, st["partition_ms"], st["partition_bytes"], st["levels"]
+        bqs.set_option("timing", 0)
+        ach = pb / (pm / 1e3) / 1e9 if pm else None
+        rows.append({"rule": rule, "name": name, "ms": round(best, 3), "keys_per_s": n / (best / 1e3),
+                     "levels": lv, "partition_keys_per_key": pb / (2 * src.element_size()) / n,
+                     "partition_GBs": ach, "partition_frac": ach / peak if ach else None})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "pivots", "metric": "keys/s and partition levels per pivot rule",
+                      "unit": "keys/s", "data": "synthetic",
+                      "config": {"n": n, "dtype": a.dtype, "dist": a.dist, "seed": a.seed,
+                                 "launch_shape": tuned},
+                      "timing": f"best of {a.steps} sorts after {a.warmup} warm-up", "rows": rows}),
+          flush=True)
+
+
 def run_serving(a):
     """Poisson sort requests (sizes 2^U(10,26), mixed dtypes) at several rates, served
     with continuous batching and with one launch per request."""
@@ -664,6 +712,8 @@ def main(argv=None):
         run_serving(a)
     elif a.workload == "matrix":
         run_matrix(a)
+    elif a.workload == "pivots":
+        run_pivots(a)
     else:
         run_ours(a)
 

@@ -157,7 +157,13 @@ int bqs_sort_noalloc(void* keys, int64_t n, int32_t dtype, bqs_stream_t stream);
 
 /* Process-wide options, read at the start of each call. */
 typedef enum {
-  BQS_OPT_PIVOT = 0,        /* 0 = median-of-3 (default), 1 = median of a sqrt(n) sample */
+  BQS_OPT_PIVOT = 0,        /* pivot rule (Sec. 4, "Different Pivot Selection Methods"):
+                               0 = median-of-3 of first, middle, last (default);
+                               1 = median-of-sqrt(n) (median-of-5-medians-of-5 below
+                               20000 keys); 2 = median-of-5; 3 = median-of-23;
+                               4 = median-of-3-medians-of-3; 5 = median-of-3-medians-
+                               of-5; 6 = median-of-5-medians-of-5.  Samples are equally
+                               spaced keys; every rule uses median-of-3 below 64 keys */
   BQS_OPT_SMALL_CUTOFF = 1, /* small-segment cutoff C, 2 .. 2048 (default 2048) */
   BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
   BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */

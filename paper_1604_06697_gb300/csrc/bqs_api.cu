@@ -227,7 +227,7 @@ int bqs_set_option(int32_t opt, int64_t value) {
   std::lock_guard<std::mutex> g(g_opt_mu);
   switch (opt) {
     case BQS_OPT_PIVOT:
-      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      if (value < 0 || value > 6) return BQS_ERR_INVALID;
       g_opt.pivot_rule = value;
       return BQS_OK;
     case BQS_OPT_SMALL_CUTOFF:

@@ -140,7 +140,7 @@ struct Params {
   Lists l;
   Ctrl* ctrl;
   int p;              // parity of the lists consumed by this level
-  int pivot_rule;     // 0 = median-of-3, 1 = median of a sqrt(n) sample
+  int pivot_rule;     // BQS_OPT_PIVOT: 0 = median-of-3, 1 = median of a sqrt(n) sample, 2..6 (Sec. 4)
   int small_cutoff;   // segments of at most this many keys go to the sorting network
   int local_cutoff;   // segments of at most this many keys are finished by one block
   int depth_limit;    // partition levels before the depth fallback pivot

@@ -77,33 +77,73 @@ __device__ Elem<KT, PAIRS> median5(Elem<KT, PAIRS>* e) {
   return e[2];
 }
 
-// Pivot rules one thread can evaluate (Sec. 2, Sec. 4): median-of-3 of (first, middle,
-// last); for the sqrt rule below 64 keys also median-of-3, below 20000 keys the
-// median-of-five-medians-of-five of 25 equally spaced keys.  Returns false when the
-// segment needs k_pivot instead (a sqrt(n) sample, or the depth-limit fallback).
+// The pivot rules of Sec. 4 ("Different Pivot Selection Methods"), BQS_OPT_PIVOT:
+//   0 median-of-3 of (first, middle, last)     4 median-of-3-medians-of-3
+//   1 median-of-sqrt(n) (see below)            5 median-of-3-medians-of-5
+//   2 median-of-5                              6 median-of-5-medians-of-5
+//   3 median-of-23
+// Samples other than rule 0's are k equally spaced keys, key i at
+// b + floor((2i+1) len / (2k)); a median of medians takes k = G*K of them in G groups
+// of K consecutive sample keys.  Every rule uses median-of-3 below 64 keys.  The
+// sqrt(n) rule takes median-of-5-medians-of-5 below 20000 keys and above that the
+// median of floor(sqrt(len))|1 spaced keys, sampled by k_pivot.
+
+// Median of K (odd) spaced keys: the middle of the sorted sample.
+template <class KT, bool PAIRS, int K>
+__device__ Elem<KT, PAIRS> median_spaced(const typename KT::U* keys, const uint32_t* vals,
+                                         int64_t b, int64_t len) {
+  Elem<KT, PAIRS> e[K];
+  for (int i = 0; i < K; ++i)
+    e[i] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (int64_t)i + 1) * len) / (2 * K));
+  for (int i = 1; i < K; ++i) {        // insertion sort of the sample
+    Elem<KT, PAIRS> x = e[i];
+    int j = i;
+    while (j > 0 && lt(x, e[j - 1])) { e[j] = e[j - 1]; --j; }
+    e[j] = x;
+  }
+  return e[K / 2];
+}
+
+// Median of G medians of K consecutive sample keys (G, K in {3, 5}).
+template <class KT, bool PAIRS, int G, int K>
+__device__ Elem<KT, PAIRS> median_of_medians(const typename KT::U* keys, const uint32_t* vals,
+                                             int64_t b, int64_t len) {
+  Elem<KT, PAIRS> m[G];
+  for (int g = 0; g < G; ++g) {
+    Elem<KT, PAIRS> e[K];
+    for (int j = 0; j < K; ++j)
+      e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (int64_t)(K * g + j) + 1) * len) / (2 * G * K));
+    m[g] = K == 3 ? median3<KT, PAIRS>(e[0], e[1], e[2]) : median5<KT, PAIRS>(e);
+  }
+  return G == 3 ? median3<KT, PAIRS>(m[0], m[1], m[2]) : median5<KT, PAIRS>(m);
+}
+
+// A pivot one thread evaluates: every rule below 20000 keys, all but sqrt(n) above.
+template <class KT, bool PAIRS>
+__device__ Elem<KT, PAIRS> rule_pivot(const typename KT::U* keys, const uint32_t* vals, int64_t b,
+                                      int64_t len, int rule) {
+  if (rule == 0 || len < 64)
+    return median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, b),
+                              load_elem<KT, PAIRS>(keys, vals, b + len / 2),
+                              load_elem<KT, PAIRS>(keys, vals, b + len - 1));
+  switch (rule) {
+    case 2: return median_spaced<KT, PAIRS, 5>(keys, vals, b, len);
+    case 3: return median_spaced<KT, PAIRS, 23>(keys, vals, b, len);
+    case 4: return median_of_medians<KT, PAIRS, 3, 3>(keys, vals, b, len);
+    case 5: return median_of_medians<KT, PAIRS, 3, 5>(keys, vals, b, len);
+    default: return median_of_medians<KT, PAIRS, 5, 5>(keys, vals, b, len);   // 1 and 6
+  }
+}
+
+// Returns false when the segment needs k_pivot instead (a sqrt(n) sample, or the
+// depth-limit fallback).
 template <class KT, bool PAIRS>
 __device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity, int depth,
                              uint64_t& pkey, uint32_t& pval) {
-  using E = Elem<KT, PAIRS>;
   if (depth >= P.depth_limit) return false;
   if (P.pivot_rule == 1 && len >= 20000) return false;
-  const typename KT::U* keys = (const typename KT::U*)P.b.key[parity];
-  const uint32_t* vals = P.b.val[parity];
-  E piv;
-  if (P.pivot_rule == 0 || len < 64) {
-    piv = median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, b),
-                             load_elem<KT, PAIRS>(keys, vals, b + len / 2),
-                             load_elem<KT, PAIRS>(keys, vals, b + len - 1));
-  } else {
-    E m[5];
-    for (int g = 0; g < 5; ++g) {
-      E e[5];
-      for (int j = 0; j < 5; ++j)
-        e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (5 * g + j) + 1) * len) / 50);
-      m[g] = median5<KT, PAIRS>(e);
-    }
-    piv = median5<KT, PAIRS>(m);
-  }
+  const Elem<KT, PAIRS> piv = rule_pivot<KT, PAIRS>((const typename KT::U*)P.b.key[parity],
+                                                    P.b.val[parity], b, len, P.pivot_rule);
   pkey = (uint64_t)KT::unord(piv.k);
   pval = piv.v;
   return true;

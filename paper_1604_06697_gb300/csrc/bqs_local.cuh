@@ -37,29 +37,6 @@ struct LocalShape {
   static constexpr size_t smem = 2 * (kbuf + vbuf);
 };
 
-// Pivot of the sub-segment keys[0, len) in shared memory, by the rules route_warp applies
-// to global segments of the same length (inline_pivot): median-of-3 of (first, middle,
-// last), or for the sqrt(n) rule from 64 keys on the median-of-5-medians-of-5 of 25
-// spaced keys; sub-segments here are shorter than the 20000 keys from which the global
-// rule takes a sqrt(n) sample.
-template <class KT, bool PAIRS>
-__device__ Elem<KT, PAIRS> local_pivot(const Params& P, const typename KT::U* keys,
-                                       const uint32_t* vals, int len) {
-  using E = Elem<KT, PAIRS>;
-  if (P.pivot_rule == 0 || len < 64)
-    return median3<KT, PAIRS>(load_elem<KT, PAIRS>(keys, vals, 0),
-                              load_elem<KT, PAIRS>(keys, vals, len / 2),
-                              load_elem<KT, PAIRS>(keys, vals, len - 1));
-  E m[5];
-  for (int g = 0; g < 5; ++g) {
-    E e[5];
-    for (int j = 0; j < 5; ++j)
-      e[j] = load_elem<KT, PAIRS>(keys, vals, ((2 * (5 * g + j) + 1) * (int64_t)len) / 50);
-    m[g] = median5<KT, PAIRS>(e);
-  }
-  return median5<KT, PAIRS>(m);
-}
-
 template <class KT, bool PAIRS, int L, int T>
 __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
   using U = typename KT::U;
@@ -124,7 +101,7 @@ __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
         const uint32_t* vv = vb(a.buf) + a.begin;
         E piv;
         if (a.depth < P.depth_limit) {
-          piv = local_pivot<KT, PAIRS>(P, kk, vv, a.len);
+          piv = rule_pivot<KT, PAIRS>(kk, vv, 0, a.len, P.pivot_rule);   // as on global levels
         } else {
           U kmin = ~U(0), kmax = 0;
           for (int i = 0; i < a.len; ++i) {

@@ -72,7 +72,12 @@ def test_options_round_trip(lib):
         with pytest.raises(bqs.BqsError):
             bqs.set_option("small_cutoff", 4096)
         with pytest.raises(bqs.BqsError):
-            bqs.set_option("pivot", 3)
+            bqs.set_option("pivot", 7)             # rules 0..6 (Sec. 4)
+        old_pivot = bqs.get_option("pivot")
+        for rule in range(7):
+            bqs.set_option("pivot", rule)
+            assert bqs.get_option("pivot") == rule
+        bqs.set_option("pivot", old_pivot)
     finally:
         bqs.set_option("small_cutoff", old)
 

@@ -334,3 +334,23 @@ def test_pairs_packed_and_fallback_networks(bqs, dtype, kind, small_sort):
         wk, wv = oracle.sort_pairs(keys, vals)
         assert_same_bits(tk.cpu().numpy(), wk)
         assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
+
+
+PIVOT_RULES = {0: "median-of-3", 1: "median-of-sqrt(n)", 2: "median-of-5", 3: "median-of-23",
+               4: "median-of-3-medians-of-3", 5: "median-of-3-medians-of-5",
+               6: "median-of-5-medians-of-5"}
+
+
+@pytest.mark.parametrize("local", [0, -1])
+@pytest.mark.parametrize("rule", sorted(PIVOT_RULES))
+def test_every_pivot_rule_sorts(bqs, rule, local):
+    # Sec. 4's pivot rules change the recursion, never the sorted output.
+    bqs.set_option("pivot", rule)
+    bqs.set_option("local_cutoff", local)
+    for dtype in DTYPES:
+        for n, dist in [(100_000, "uniform"), (300_001, "mod_sqrt"), (1 << 20, "sorted"),
+                        (70_001, "reversed"), (50_000, "all_equal"), (1 << 21, "swapped_1pct")]:
+            a = inputs.make_keys(n, dtype, dist, seed=rule + 1)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+            st = bqs.stats()
+            assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n
