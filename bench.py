@@ -49,9 +49,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="sort",
-                    choices=["sort", "pairs", "batched", "serving", "matrix", "pivots"],
-                    help="sort (the default headline line), pairs, batched, serving, matrix or "
-                         "pivots")
+                    choices=["sort", "pairs", "batched", "serving", "matrix", "pivots",
+                             "structured"],
+                    help="sort (the default headline line), pairs, batched, serving, matrix, "
+                         "pivots or structured")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and use --tile/--small/--local instead")
@@ -581,8 +582,9 @@ def run_batched(a):
         "speedup_vs_per_array": base_ms / (ms / a.steps), "sorted_check": ok}), flush=True)
 
 
-def run_matrix(a):
-    """2^24 and 2^28 keys x int32/int64/float64 x the six distributions (seed 1)."""
+def run_matrix(a, dists=None, sizes=(24, 28), name="matrix"):
+    """2^24 and 2^28 keys x int32/int64/float64 x the six distributions (seed 1); with
+    dists/sizes given, those instead (the structured inputs)."""
     import torch
 
     from paper_1604_06697_gb300 import build as _build
@@ -593,11 +595,11 @@ def run_matrix(a):
     bqs.set_option("pivot", 1)
     rows = []
     peak, _ = measured_peak_gbs()
-    for log2n in (24, 28):
+    for log2n in sizes:
         n = 1 << log2n
         for dtype in ("int32", "int64", "float64"):
             autotune.tune(dtype, n, kind="sort")
-            for dist in inputs.DISTRIBUTIONS:
+            for dist in (dists or inputs.DISTRIBUTIONS):
                 src = torch.from_numpy(inputs.make_keys(n, dtype, dist, 1)).cuda()
                 work = torch.empty_like(src)
                 for _ in range(a.warmup):
@@ -618,7 +620,7 @@ def run_matrix(a):
                              "partition_GBs": ach, "partition_frac": ach / peak if ach else None})
                 print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
                 del src, work
-    print(json.dumps({"workload": "matrix", "metric": "keys/s per size x dtype x distribution",
+    print(json.dumps({"workload": name, "metric": "keys/s per size x dtype x distribution",
                       "unit": "keys/s", "timing": f"best of {a.steps} sorts after {a.warmup} warm-up",
                       "data": "synthetic", "rows": rows}), flush=True)
 
@@ -714,6 +716,9 @@ def main(argv=None):
         run_matrix(a)
     elif a.workload == "pivots":
         run_pivots(a)
+    elif a.workload == "structured":
+        from paper_1604_06697_gb300 import inputs
+        run_matrix(a, dists=inputs.EXTRA_DISTRIBUTIONS, sizes=(a.log2n,), name="structured")
     else:
         run_ours(a)
 

@@ -26,6 +26,12 @@ _M2 = np.uint64(0x94D049BB133111EB)
 _CHUNK = 1 << 23
 
 DISTRIBUTIONS = ("uniform", "sorted", "reversed", "mod_sqrt", "all_equal", "swapped_1pct")
+# The structured, duplicate-heavy inputs of the paper's further experiments (Sec. 4 and
+# Appendix A): A[i] = i mod floor(sqrt(n)); i^2 + n/2 mod n; i^8 + n/2 mod n; sorted
+# with k random swaps of neighbouring elements (k = sqrt(n), k = n); zeros then ones;
+# random zeros and ones.
+EXTRA_DISTRIBUTIONS = ("i_mod_sqrt", "i2_half_mod", "i8_half_mod", "adj_swaps_sqrt", "adj_swaps_n",
+                       "half_01", "random_01")
 DTYPES = ("int32", "int64", "float64")
 
 
@@ -93,7 +99,54 @@ def make_keys(n: int, dtype: str = "int32", dist: str = "uniform", seed: int = 0
             for x, y in zip(u, v):   # sequential swaps, in draw order
                 a[x], a[y] = a[y], a[x]
         return a.astype(npd)
-    raise ValueError(f"dist must be one of {DISTRIBUTIONS}")
+    if dist in EXTRA_DISTRIBUTIONS:
+        return _make_structured(n, npd, dist, seed)
+    raise ValueError(f"dist must be one of {DISTRIBUTIONS + EXTRA_DISTRIBUTIONS}")
+
+
+def _power_half_mod(n: int, e: int) -> np.ndarray:
+    """A[i] = i^e + n/2 mod n, by repeated squaring mod n (n <= 2^32)."""
+    out = np.empty(n, dtype=np.int64)
+    nn = np.uint64(max(n, 1))
+    for c0 in range(0, n, _CHUNK):
+        c1 = min(n, c0 + _CHUNK)
+        x = np.arange(c0, c1, dtype=np.uint64) % nn
+        p = np.ones_like(x)
+        b, k = x, e
+        while k:
+            if k & 1:
+                p = (p * b) % nn
+            b = (b * b) % nn
+            k >>= 1
+        out[c0:c1] = ((p + np.uint64(n // 2)) % nn).astype(np.int64)
+    return out
+
+
+def _make_structured(n: int, npd, dist: str, seed: int) -> np.ndarray:
+    if dist == "i_mod_sqrt":
+        return (np.arange(n, dtype=np.int64) % max(1, math.isqrt(n))).astype(npd)
+    if dist == "i2_half_mod":
+        return _power_half_mod(n, 2).astype(npd)
+    if dist == "i8_half_mod":
+        return _power_half_mod(n, 8).astype(npd)
+    if dist in ("adj_swaps_sqrt", "adj_swaps_n"):
+        a = np.arange(n, dtype=np.int64)
+        k = math.isqrt(n) if dist == "adj_swaps_sqrt" else n
+        if n > 1 and k:
+            pos = (splitmix64(seed, k, stream=2) % np.uint64(n - 1)).astype(np.int64).tolist()
+            lst = a.tolist()
+            for j in pos:            # swaps of neighbours, in draw order
+                lst[j], lst[j + 1] = lst[j + 1], lst[j]
+            a = np.array(lst, dtype=np.int64)
+        return a.astype(npd)
+    if dist == "half_01":
+        return (np.arange(n, dtype=np.int64) >= n // 2).astype(npd)
+    # random_01
+    out = np.empty(n, dtype=npd)
+    for c0 in range(0, n, _CHUNK):
+        c1 = min(n, c0 + _CHUNK)
+        out[c0:c1] = (splitmix64(seed, c1 - c0, start=c0) >> np.uint64(63)).astype(npd)
+    return out
 
 
 def make_pairs(n: int, seed: int = 1, key_range: int = 1 << 20):

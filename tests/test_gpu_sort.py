@@ -354,3 +354,14 @@ def test_every_pivot_rule_sorts(bqs, rule, local):
             assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
             st = bqs.stats()
             assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n
+
+
+@pytest.mark.parametrize("pivot", [0, 1])
+@pytest.mark.parametrize("dist", inputs.EXTRA_DISTRIBUTIONS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_structured_distributions(bqs, dtype, dist, pivot):
+    # The duplicate-heavy and nearly sorted inputs of the paper's further experiments.
+    bqs.set_option("pivot", pivot)
+    for n in (300_001, 1 << 20):
+        a = inputs.make_keys(n, dtype, dist, seed=n)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
