@@ -50,9 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="sort",
                     choices=["sort", "pairs", "batched", "serving", "matrix", "pivots",
-                             "structured"],
+                             "structured", "records"],
                     help="sort (the default headline line), pairs, batched, serving, matrix, "
-                         "pivots or structured")
+                         "pivots, structured or records")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and use --tile/--small/--local instead")
@@ -672,6 +672,57 @@ def run_pivots(a):
           flush=True)
 
 
+def run_records(a):
+    """Sec. 4's wide element types: Record (21 int32, compared by the first) and Vector
+    (10 float64, compared by the norm), sorted indirectly by bqs_sort_records."""
+    import torch
+
+    from paper_1604_06697_gb300 import build as _build
+    _build.build()
+    import paper_1604_06697_gb300 as bqs
+    from paper_1604_06697_gb300 import inputs
+
+    n = 1 << a.log2n
+    bqs.set_option("pivot", 1)
+    rows = []
+    for name, kind, rb, count in (("Record", bqs.KEY_I32_FIELD, 84, 1),
+                                  ("Vector", bqs.KEY_F64_SQNORM, 80, 10)):
+        r = inputs.splitmix64(a.seed, n * rb // 4)
+        host = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        del r
+        if kind == bqs.KEY_F64_SQNORM:
+            hv = host.view(np.float64)
+            for c0 in range(0, hv.size, 1 << 24):
+                c1 = min(hv.size, c0 + (1 << 24))
+                hv[c0:c1] = 2.0 * inputs.unit_double(inputs.splitmix64(a.seed + 1, c1 - c0, start=c0)) - 1.0
+        src = torch.from_numpy(host.view(np.uint8)).cuda()
+        work = torch.empty_like(src)
+        for _ in range(a.warmup):
+            work.copy_(src)
+            bqs.sort_records(work, rb, kind, 0, count)
+        best = float("inf")
+        for _ in range(a.steps):
+            work.copy_(src)
+            best = min(best, _cuda_ms(lambda: bqs.sort_records(work, rb, kind, 0, count)))
+        w = work.view(torch.int32).view(n, rb // 4)
+        if kind == bqs.KEY_I32_FIELD:
+            k = w[:, 0]
+        else:
+            v = work.view(torch.float64).view(n, rb // 8)
+            k = (v * v).sum(dim=1)
+        ok = bool((k[1:] >= k[:-1]).all()) if kind == bqs.KEY_I32_FIELD else \
+            bool((k[1:] >= k[:-1] * (1 - 1e-12)).all())
+        rows.append({"element": name, "record_bytes": rb, "n": n, "ms": round(best, 3),
+                     "elements_per_s": n / (best / 1e3),
+                     "record_GBs": n * rb / (best / 1e3) / 1e9, "ordered_check": ok})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del src, work
+    print(json.dumps({"workload": "records", "metric": "elements/s, indirect sort of wide elements",
+                      "unit": "elements/s", "data": "synthetic",
+                      "timing": f"best of {a.steps} sorts after {a.warmup} warm-up", "rows": rows}),
+          flush=True)
+
+
 def run_serving(a):
     """Poisson sort requests (sizes 2^U(10,26), mixed dtypes) at several rates, served
     with continuous batching and with one launch per request."""
@@ -716,6 +767,8 @@ def main(argv=None):
         run_matrix(a)
     elif a.workload == "pivots":
         run_pivots(a)
+    elif a.workload == "records":
+        run_records(a)
     elif a.workload == "structured":
         from paper_1604_06697_gb300 import inputs
         run_matrix(a, dists=inputs.EXTRA_DISTRIBUTIONS, sizes=(a.log2n,), name="structured")

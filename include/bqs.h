@@ -155,6 +155,38 @@ int bqs_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, bqs_str
  */
 int bqs_sort_noalloc(void* keys, int64_t n, int32_t dtype, bqs_stream_t stream);
 
+/* Keys of wide elements for bqs_sort_records. */
+typedef enum {
+  BQS_KEY_I32_FIELD = 0,   /* the int32 field at key_offset (the paper's Record type) */
+  BQS_KEY_F64_SQNORM = 1   /* squared Euclidean norm of the key_count doubles starting at
+                              key_offset (the paper's Vector type, compared by its norm),
+                              summed in component order with every product and sum
+                              rounded to double (no fused multiply-add) */
+} bqs_record_key;
+
+/*
+ * Sorts n fixed-size records in place by a key taken from each record: the wide
+ * element types of Sec. 4 ("Record": 21 ints compared by the first one; "Vector": 10
+ * doubles compared by their norm).  The sort is indirect: each record's key is paired
+ * with its index, the (key, index) pairs are sorted like bqs_sort_pairs, and every
+ * record is then moved once to its sorted place.  Records with equal keys keep their
+ * input order (the index breaks ties), so the output is unique.
+ *
+ *   records       device, n * record_bytes bytes, caller-owned, sorted in place;
+ *                 4-byte aligned (8-byte aligned for BQS_KEY_F64_SQNORM)
+ *   record_bytes  a multiple of 4 (of 8 for BQS_KEY_F64_SQNORM)
+ *   key_kind      a bqs_record_key; key_offset: byte offset of the key (component)
+ *                 in a record, aligned to its type; key_count: doubles in the norm
+ *                 (ignored for BQS_KEY_I32_FIELD)
+ * Scratch (keys, indices and one copy of the records) comes from cudaMallocAsync on
+ * `stream` and is returned on it.  n <= 2^32-1.  Errors: BQS_ERR_INVALID for bad
+ * sizes, offsets or alignment; BQS_ERR_NOMEM; BQS_ERR_CUDA.  NaN components are outside
+ * the contract.  Synchronous with respect to `stream` between partition levels, like
+ * bqs_sort.
+ */
+int bqs_sort_records(void* records, int64_t n, int32_t record_bytes, int32_t key_kind,
+                     int32_t key_offset, int32_t key_count, bqs_stream_t stream);
+
 /* Process-wide options, read at the start of each call. */
 typedef enum {
   BQS_OPT_PIVOT = 0,        /* pivot rule (Sec. 4, "Different Pivot Selection Methods"):

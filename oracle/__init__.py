@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(
-            ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+            ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -56,6 +56,8 @@ def _load():
         lib.oracle_partition_by_value.restype = i64
         lib.oracle_select.argtypes = [vp, i64, i32, i64, vp]
         lib.oracle_select.restype = ctypes.c_int
+        lib.oracle_record_keys.argtypes = [vp, i64, i32, i32, i32, i32, vp]
+        lib.oracle_record_keys.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -68,7 +70,8 @@ def use_library(path: str) -> None:
     _load()  # make sure the signatures of the default build are known
     lib = ctypes.CDLL(path)
     for name in ("oracle_sort", "oracle_sort_pairs", "oracle_sort_segmented",
-                 "oracle_block_partition", "oracle_partition_by_value", "oracle_select"):
+                 "oracle_block_partition", "oracle_partition_by_value", "oracle_select",
+                 "oracle_record_keys"):
         f, g = getattr(lib, name), getattr(_lib, name)
         f.argtypes, f.restype = g.argtypes, g.restype
     _lib = lib
@@ -178,3 +181,30 @@ def ord_f64(x: np.ndarray) -> np.ndarray:
     u = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
     neg = (u >> np.uint64(63)).astype(bool)
     return np.where(neg, ~u, u | np.uint64(1 << 63))
+
+
+def record_keys(records: np.ndarray, record_bytes: int, kind: int, offset: int = 0,
+                count: int = 1) -> np.ndarray:
+    """Keys of fixed-size records (bytes, n * record_bytes): kind 0 = the int32 field at
+    ``offset``; kind 1 = the squared norm of ``count`` doubles from ``offset``."""
+    rec = np.ascontiguousarray(records).view(np.uint8)
+    n = rec.size // record_bytes
+    keys = np.empty(n, dtype=np.int32 if kind == 0 else np.float64)
+    rc = _load().oracle_record_keys(rec.ctypes.data, n, record_bytes, kind, offset, count,
+                                    keys.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_record_keys rejected its arguments")
+    return keys
+
+
+def sort_records(records: np.ndarray, record_bytes: int, kind: int, offset: int = 0,
+                 count: int = 1) -> np.ndarray:
+    """Records (bytes, n * record_bytes) sorted by their keys, ties by input position:
+    the (key, index) pairs are sorted by the paper's algorithm, then the records are
+    moved to their places."""
+    rec = np.ascontiguousarray(records).view(np.uint8)
+    n = rec.size // record_bytes
+    keys = record_keys(rec, record_bytes, kind, offset, count)
+    _, order = sort_pairs(keys, np.arange(n, dtype=np.uint32))
+    return rec.reshape(n, record_bytes)[order.astype(np.int64)].reshape(-1)
+

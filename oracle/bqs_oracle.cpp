@@ -485,4 +485,37 @@ int64_t oracle_partition_by_value(const void* keys, int64_t n, int32_t dtype, co
   }
 }
 
+// Keys of the wide element types of Sec. 4 ("Different Element Types"): kind 0 = the
+// int32 field at byte `offset` of each record (Record: compared by its first field);
+// kind 1 = the squared Euclidean norm of the `count` doubles at `offset` (Vector:
+// compared by its norm), summed in component order, each product and sum rounded on
+// its own (the library is compiled without contraction into fused multiply-adds).
+// Sorting the records is then sorting the (key, record index) pairs -- ties broken by
+// the index -- and moving every record to its place.
+int oracle_record_keys(const void* records, int64_t n, int32_t record_bytes, int32_t kind,
+                       int32_t offset, int32_t count, void* keys) {
+  if (n < 0 || !records || !keys || record_bytes <= 0) return -1;
+  const unsigned char* rec = static_cast<const unsigned char*>(records);
+  for (int64_t i = 0; i < n; ++i) {
+    const unsigned char* r = rec + i * record_bytes + offset;
+    if (kind == 0) {
+      int32_t v;
+      std::memcpy(&v, r, 4);
+      static_cast<int32_t*>(keys)[i] = v;
+    } else if (kind == 1) {
+      double s = 0.0;
+      for (int32_t c = 0; c < count; ++c) {
+        double x;
+        std::memcpy(&x, r + 8 * c, 8);
+        const double sq = x * x;
+        s = s + sq;
+      }
+      static_cast<double*>(keys)[i] = s;
+    } else {
+      return -1;
+    }
+  }
+  return 0;
+}
+
 }  // extern "C"

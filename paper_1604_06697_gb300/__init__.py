@@ -75,6 +75,26 @@ def sort_noalloc(keys, stream=None):
     return keys
 
 
+KEY_I32_FIELD, KEY_F64_SQNORM = 0, 1
+
+
+def sort_records(records, record_bytes, key_kind, key_offset=0, key_count=1, stream=None):
+    """Sorts fixed-size records in place by a key taken from each record.
+
+    ``records`` is a contiguous CUDA tensor holding n * record_bytes bytes (any dtype).
+    key_kind KEY_I32_FIELD: the int32 at byte ``key_offset``; KEY_F64_SQNORM: the squared
+    norm of ``key_count`` doubles from ``key_offset``.  Equal keys keep their order.
+    """
+    _require_cuda(records)
+    nbytes = records.numel() * records.element_size()
+    if record_bytes <= 0 or nbytes % record_bytes:
+        raise ValueError("records must hold a whole number of records")
+    _check(_native.lib().bqs_sort_records(records.data_ptr(), nbytes // record_bytes, record_bytes,
+                                          key_kind, key_offset, key_count,
+                                          _stream_ptr(records, stream)), "bqs_sort_records")
+    return records
+
+
 def sort_pairs(keys, vals, stream=None):
     """Sorts (key, uint32 payload) pairs in place by (key, payload).
 

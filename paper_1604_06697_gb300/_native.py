@@ -38,6 +38,7 @@ SIGNATURES = {
     "bqs_sort_batched": (ctypes.c_int, [c_vp, c_i64, c_vp, c_i64, c_i32, c_vp]),
     "bqs_sort_pairs": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_vp]),
     "bqs_sort_noalloc": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp]),
+    "bqs_sort_records": (ctypes.c_int, [c_vp, c_i64, c_i32, c_i32, c_i32, c_i32, c_vp]),
     "bqs_set_option": (ctypes.c_int, [c_i32, c_i64]),
     "bqs_get_option": (ctypes.c_int, [c_i32, ctypes.POINTER(c_i64)]),
     "bqs_workspace_bytes": (ctypes.c_int, [c_i64, c_i32, c_i32, c_i64, ctypes.POINTER(c_i64)]),

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbqs.so")
 
-SOURCES = ["bqs_api.cu", "bqs_i32.cu", "bqs_i64.cu", "bqs_f64.cu", "bqs_noalloc.cu"]
+SOURCES = ["bqs_api.cu", "bqs_i32.cu", "bqs_i64.cu", "bqs_f64.cu", "bqs_noalloc.cu", "bqs_records.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -45,6 +45,9 @@ MUTANTS = [
     ("depth limit", "2 * floor_log2(n) + 3", "2 * floor_log2(n) + 300"),
     ("value partition", "else out[hi++] = keys[i];", "else out[hi++] = pivot;"),
     ("order statistic index", "*(int32_t*)out = a[k];", "*(int32_t*)out = a[k > 0 ? k - 1 : k];"),
+    ("record norm components", "for (int32_t c = 0; c < count; ++c) {\n        double x;",
+     "for (int32_t c = 1; c < count; ++c) {\n        double x;"),
+    ("record key field", "std::memcpy(&v, r, 4);", "std::memcpy(&v, r + 4, 4);"),
 ]
 
 _RUNNER = r"""
@@ -71,6 +74,7 @@ pins = [
     lambda: P.test_block_partition_large_and_compares_each_element_once(),
     lambda: P.test_default_depth_limit_is_the_papers(1 << 10),
     lambda: P.test_select_is_the_order_statistic("int32"),
+    lambda: P.test_record_keys_follow_their_definition(),
 ]
 for i, pin in enumerate(pins):
     try:

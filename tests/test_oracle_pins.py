@@ -316,3 +316,45 @@ def test_segmented_is_per_segment_sort():
     got = oracle.sort_segmented(keys, off)
     for i in range(64):
         assert np.array_equal(got[off[i]:off[i + 1]], np.sort(keys[off[i]:off[i + 1]]))
+
+
+# ---- wide element types (Sec. 4, "Different Element Types") ------------------------------
+
+def _records(n, rb, seed, kind):
+    r = inputs.splitmix64(seed, n * rb // 4)
+    rec = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.uint8).copy()
+    if kind == 0:       # Record: first field with many ties
+        f = rec.view(np.int32).reshape(n, rb // 4)
+        f[:, 0] = (inputs.splitmix64(seed + 1, n) % np.uint64(max(1, n // 4))).astype(np.int32)
+    else:               # Vector: doubles in [-1, 1), some vectors repeated (equal norms)
+        v = rec.view(np.float64).reshape(n, rb // 8)
+        v[:] = 2.0 * inputs.unit_double(inputs.splitmix64(seed + 2, v.size)).reshape(v.shape) - 1.0
+        v[1::7] = v[0::7][: v[1::7].shape[0]]
+    return rec
+
+
+def test_record_keys_follow_their_definition():
+    rb = 84
+    rec = _records(500, rb, 1, 0)
+    keys = oracle.record_keys(rec, rb, 0)
+    assert np.array_equal(keys, rec.view(np.int32).reshape(500, 21)[:, 0])
+    rb = 80
+    rec = _records(300, rb, 2, 1)
+    keys = oracle.record_keys(rec, rb, 1, 0, 10)
+    v = rec.view(np.float64).reshape(300, 10)
+    for i in range(300):
+        s = 0.0
+        for c in range(10):      # Python floats: every product and sum rounded on its own
+            s = s + v[i, c] * v[i, c]
+        assert keys[i] == s
+    assert oracle.record_keys(rec, rb, 1, 16, 3)[5] == sum(x * x for x in v[5, 2:5])
+
+
+@pytest.mark.parametrize("kind,rb,count", [(0, 84, 1), (1, 80, 10)])
+def test_sorted_records_are_ordered_by_key_then_position(kind, rb, count):
+    n = 2000
+    rec = _records(n, rb, 7, kind)
+    got = oracle.sort_records(rec, rb, kind, 0, count).reshape(n, rb)
+    keys = oracle.record_keys(rec, rb, kind, 0, count)
+    order = sorted(range(n), key=lambda i: (keys[i], i))
+    assert np.array_equal(got, rec.reshape(n, rb)[order])
