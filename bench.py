@@ -60,6 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--small", type=int, default=None)
     ap.add_argument("--local", type=int, default=None)
     ap.add_argument("--small-sort", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--overlap", type=int, default=None, choices=[0, 1])
     return ap.parse_args(argv)
 
 
@@ -299,7 +300,7 @@ def run_ours(a):
         tuned = autotune.tune(a.dtype, n, kind="sort")["config"]
     else:
         for name, v in (("tile", a.tile), ("small_cutoff", a.small), ("local_cutoff", a.local),
-                        ("small_sort", a.small_sort)):
+                        ("small_sort", a.small_sort), ("overlap", a.overlap)):
             if v is not None:
                 bqs.set_option(name, v)
     host = inputs.make_keys(n, a.dtype, a.dist, a.seed)
@@ -434,6 +435,7 @@ def run_ours(a):
         "algorithmic_bytes_per_launch": part_bytes / max(1, part_launches),
         "avg_launch_ms": part_ms / max(1, part_launches),
         "frac_of_8tbs_spec": (achieved / 8000.0) if achieved else None,
+        "concurrent_with_networks": bool(bqs.get_option("overlap")),
     }
     if rank == 0:
         line = {

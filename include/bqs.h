@@ -218,7 +218,7 @@ typedef enum {
                                pinned per-level flag a few levels behind (sorts and
                                segmented sorts; bqs_partition and bqs_sort_noalloc
                                always use 0) */
-  BQS_OPT_SMALL_SORT = 9    /* sorting network for segments of 257 .. small-cutoff keys:
+  BQS_OPT_SMALL_SORT = 9,   /* sorting network for segments of 257 .. small-cutoff keys:
                                0 (default) = key-only: one warp per segment up to 1024
                                (512 for 64-bit keys) keys and one 64-thread (32-bit) or
                                128-thread (64-bit) block above; key-value: the pairs
@@ -226,6 +226,12 @@ typedef enum {
                                payload) where the segment's key range allows (always
                                for 32-bit keys), one 256-thread block otherwise;
                                1 = one 256-thread block per segment. */
+  BQS_OPT_OVERLAP = 10      /* 1: the sorting networks of each level run on a second
+                               stream of the library's, beside the next partition
+                               levels (they touch disjoint key ranges); the call's
+                               stream waits for them before the call returns.  0 (the
+                               default): everything on the caller's stream.  Used when
+                               the host reads the counts after every level. */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

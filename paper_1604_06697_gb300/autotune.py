@@ -3,7 +3,8 @@
 Chooses, for one workload class (dtype, size bucket, single array or batch), the
 partition tile variant (threads x keys per thread), the small-segment cutoff, the
 small-segment network shape (one warp / warp group per segment, or one 256-thread
-block) and the single-block local-partitioning cutoff by timing every candidate on a synthetic input
+block), whether the networks run on a second stream beside the partitions, and the
+single-block local-partitioning cutoff by timing every candidate on a synthetic input
 of that class with CUDA events.  Results are cached in a JSON file keyed by GPU
 name, dtype, workload kind and log2 size bucket, so a later process applies the
 choice without re-timing.  The tuner only sets the library's options; every
@@ -22,7 +23,8 @@ TILES = (0, 1, 2, 3, 4, 5)     # TMA partition variants (see bqs_set_option(BQS_
 SMALL_CUTOFFS = (256, 1024, 2048)
 LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
 SMALL_SORTS = (0, 1)           # warp / warp-group networks, or 256-thread block networks
-KNOBS = ("tile", "small_cutoff", "local_cutoff", "small_sort")
+OVERLAPS = (0, 1)              # networks on the call's stream, or beside the partitions
+KNOBS = ("tile", "small_cutoff", "local_cutoff", "small_sort", "overlap")
 
 
 def default_cache_path() -> str:
@@ -129,9 +131,9 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
-    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w)
-                           for t, s, l, w in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
-                                                               SMALL_SORTS)]
+    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o)
+                           for t, s, l, w, o in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
+                                                                  SMALL_SORTS, OVERLAPS)]
     try:
         for cfg in cands:
             apply(cfg)

@@ -113,6 +113,27 @@ std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() {
   return t_events[current_device_slot()];
 }
 
+thread_local cudaStream_t t_side_stream[kMaxDevices];
+thread_local cudaEvent_t t_side_events[kMaxDevices][2];
+
+cudaStream_t side_stream() {
+  cudaStream_t& s = t_side_stream[current_device_slot()];
+  if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  return s;
+}
+
+cudaEvent_t side_event(int i) {
+  cudaEvent_t& e = t_side_events[current_device_slot()][i & 1];
+  if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+
 cudaEvent_t counts_event() {
   cudaEvent_t& e = t_counts_event[current_device_slot()];
   if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -266,6 +287,10 @@ int bqs_set_option(int32_t opt, int64_t value) {
       if (value < 0 || value > 1) return BQS_ERR_INVALID;
       g_opt.small_sort = value;
       return BQS_OK;
+    case BQS_OPT_OVERLAP:
+      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      g_opt.overlap = value;
+      return BQS_OK;
     default:
       return BQS_ERR_UNSUPPORTED;
   }
@@ -285,6 +310,7 @@ int bqs_get_option(int32_t opt, int64_t* value) {
     case BQS_OPT_TEST_STALL: *value = g_opt.test_stall; return BQS_OK;
     case BQS_OPT_LEVEL_LOOP: *value = g_opt.level_loop; return BQS_OK;
     case BQS_OPT_SMALL_SORT: *value = g_opt.small_sort; return BQS_OK;
+    case BQS_OPT_OVERLAP: *value = g_opt.overlap; return BQS_OK;
     default: return BQS_ERR_UNSUPPORTED;
   }
 }

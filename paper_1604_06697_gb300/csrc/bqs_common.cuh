@@ -152,6 +152,10 @@ struct Params {
   int test_stall;       // failure-path test: one tile is never requested
   int small_sort;       // 0: warp / warp-group networks for key-only sorts; 1: 256-thread blocks
   int group_min;        // small segments longer than this go to the `group` list
+  // Network launches on a second stream take their list lengths from here (the
+  // device-side counts of their lists may already be cleared for the next level).
+  int fixed_counts;
+  uint32_t n_tiny, n_small, n_group;
 };
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {

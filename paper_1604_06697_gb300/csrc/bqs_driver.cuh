@@ -576,8 +576,32 @@ int run_call(const Call& c, Stats& st) {
   // partitions and the allocation-free entry point (which creates no CUDA objects)
   // synchronise the stream at the end of each level instead.
   const cudaEvent_t counts_ev = (c.partition_only || c.fixed_ws) ? nullptr : counts_event();
+  // BQS_OPT_OVERLAP: each level's networks run on a second stream, beside the partition
+  // levels (disjoint key ranges).  They read their list lengths from the kernel
+  // arguments; `ready` marks the end of the bookkeeping that wrote their runs, `done`
+  // their end, which the next bookkeeping (it rewrites those runs) and the call's
+  // return wait for.
+  cudaStream_t s1 = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  if (c.opt.overlap && counts_ev) {
+    s1 = side_stream();
+    ready = side_event(0);
+    done = side_event(1);
+    if (!s1 || !ready || !done) s1 = nullptr;
+  }
+  bool side_work = false;
+  auto join = [&]() {
+    if (side_work) cudaStreamWaitEvent(s, done, 0);
+  };
+  // Every way out of the call (errors included) makes the call's stream wait for the
+  // networks before the scratch is returned on it.
+  struct Join {
+    decltype(join)& f;
+    ~Join() { f(); }
+  } join_on_exit{join};
+  if (s1) BQS_CK(cudaEventRecord(ready, s));
   for (int level = 0;; ++level) {
-    if (level > max_levels) return kErrInternal;
+    if (level > max_levels) { join(); return kErrInternal; }
     P.p = level & 1;
     const uint32_t nlarge = (uint32_t)cur.large, ntiles = (uint32_t)(cur.large >> 32);
     if (nlarge) {
@@ -604,6 +628,29 @@ int run_call(const Call& c, Stats& st) {
       var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s);
       P.test_stall = 0;
       if (timing) BQS_CK(cudaEventRecord(e1, s));
+      if (side_work) BQS_CK(cudaStreamWaitEvent(s, done, 0));   // the previous level's networks
+    }
+    if (s1 && (cur.tiny || cur.small || cur.group)) {
+      // This level's networks, beside this and the next partition level.
+      BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
+      Params Q = P;
+      Q.fixed_counts = 1;
+      Q.n_tiny = cur.tiny;
+      Q.n_small = cur.small;
+      Q.n_group = cur.group;
+      if (cur.tiny) {
+        st.small_segments += cur.tiny;
+        k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s1>>>(Q, Q.p);
+        st.kernel_launches += 1;
+      }
+      if (cur.small || cur.group) {
+        st.small_segments += cur.small + cur.group;
+        st.kernel_launches += launch_small<KT, PAIRS>(Q, Q.p, cur.small, cur.group, false, s1);
+      }
+      BQS_CK(cudaEventRecord(done, s1));
+      side_work = true;
+    }
+    if (nlarge) {
       k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
       st.kernel_launches += 2;
     } else if (cur.local) {
@@ -616,6 +663,7 @@ int run_call(const Call& c, Stats& st) {
       st.kernel_launches += 1;
     }
     const bool more = nlarge || cur.local;
+    if (s1 && more) BQS_CK(cudaEventRecord(ready, s));   // the next level's runs are written
     if (more && counts_ev) {
       // The next level's counts are final once bookkeeping and local partitioning have
       // run: read them back now, while this level's fills and sorting networks still
@@ -627,12 +675,12 @@ int run_call(const Call& c, Stats& st) {
       k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
-    if (cur.tiny) {
+    if (!s1 && cur.tiny) {
       st.small_segments += cur.tiny;
       k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
-    if (cur.small || cur.group) {
+    if (!s1 && (cur.small || cur.group)) {
       st.small_segments += cur.small + cur.group;
       st.kernel_launches += launch_small<KT, PAIRS>(P, P.p, cur.small, cur.group, false, s);
     }
@@ -645,7 +693,7 @@ int run_call(const Call& c, Stats& st) {
       BQS_CK(cudaStreamSynchronize(s));
     }
     host_fresh = true;
-    if (host->status) return status_code(host->status);
+    if (host->status) { join(); return status_code(host->status); }
     if (c.partition_only) {
       // split = #(< pivot); the cursor of the single segment holds it.
       unsigned long long cursor = 0;
@@ -656,6 +704,7 @@ int run_call(const Call& c, Stats& st) {
     }
     cur = host->lists[P.p ^ 1];
   }
+  join();   // the call's stream holds every kernel of the sort from here on
   if (host_fresh) {
     st.moved_keys = (int64_t)host->moved_keys;
     st.equal_keys = (int64_t)host->equal_keys;

@@ -31,6 +31,7 @@ struct Options {
   int64_t test_stall = 0;      // 1: the next sort's first partition launch stalls one tile
   int64_t level_loop = 0;      // 1: the host enqueues levels ahead instead of reading counts
   int64_t small_sort = 0;      // 1: 256-thread block networks for every small segment
+  int64_t overlap = 0;         // 1: sorting networks on a second stream, beside the partitions
 };
 
 struct Call {
@@ -69,6 +70,10 @@ void prepare_mempool();
 Ctrl* pinned_ctrl();
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();   // of the current device
 cudaEvent_t counts_event();     // the calling thread's, on the current device (null on failure)
+// The calling thread's second stream and its two events on the current device (null on
+// failure): networks run there beside the partition levels (BQS_OPT_OVERLAP).
+cudaStream_t side_stream();
+cudaEvent_t side_event(int i);
 
 // Implemented in the per-dtype translation units.
 int run_i32(const Call& c, Stats& st);

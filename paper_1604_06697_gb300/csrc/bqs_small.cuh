@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_small_warp(Params P, int p) {
   p = level_parity(P, p);
   __shared__ __align__(16) U s_x[8][kWarpSortMax];
   __shared__ __align__(16) uint32_t s_y[8][PAIRS ? kWarpSortMax : 1];
-  const unsigned int count = min(P.ctrl->lists[p].tiny, P.l.cap_run);
+  const unsigned int count = min(P.fixed_counts ? P.n_tiny : P.ctrl->lists[p].tiny, P.l.cap_run);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (unsigned int s = blockIdx.x * 8 + warp; s < count; s += gridDim.x * 8) {
     const Run r = P.l.tiny[p][s];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
   static_assert(kMax >= 512, "launched only for key-only sorts");
   p = level_parity(P, p);
   __shared__ __align__(16) U s_x[4][staging_entries<U, kMax / 32, 32>()];
-  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  const unsigned int count = min(P.fixed_counts ? P.n_small : P.ctrl->lists[p].small, P.l.cap_run);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (unsigned int s = blockIdx.x * 4 + warp; s < count; s += gridDim.x * 4) {
     const Run r = P.l.small[p][s];
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<K
   static_assert(!PAIRS, "launched only for key-only sorts");
   p = level_parity(P, p);
   __shared__ __align__(16) U s_x[staging_entries<U, G::RMAX, G::T>()];
-  const unsigned int count = min(P.ctrl->lists[p].group, P.l.cap_run);
+  const unsigned int count = min(P.fixed_counts ? P.n_group : P.ctrl->lists[p].group, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
     const Run r = P.l.group[p][s];
     if (r.len * 2 <= kMaxSmall) group_sort_run<KT, G::RMAX / 2, G::T>(P, r, threadIdx.x, s_x);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128, 4) k_small_pairs_packed(Params P, int p) 
   p = level_parity(P, p);
   __shared__ __align__(16) uint64_t s_w[staging_entries<uint64_t, kMaxSmall / T, T>()];
   __shared__ U s_red[2 * (T / 32)];
-  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  const unsigned int count = min(P.fixed_counts ? P.n_small : P.ctrl->lists[p].small, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
     const Run r = P.l.small[p][s];
     U kmin;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) k_small_block(Params P, int p) {
   __shared__ __align__(16) U s_x[kMaxSmall];
   __shared__ __align__(16) uint32_t s_y[PAIRS ? kMaxSmall : 1];
   __shared__ U s_red[PAIRS ? 16 : 1];
-  const unsigned int count = min(P.ctrl->lists[p].small, P.l.cap_run);
+  const unsigned int count = min(P.fixed_counts ? P.n_small : P.ctrl->lists[p].small, P.l.cap_run);
   for (unsigned int s = blockIdx.x; s < count; s += gridDim.x) {
     const Run r = P.l.small[p][s];
     if constexpr (PAIRS) {

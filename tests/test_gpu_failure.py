@@ -26,13 +26,15 @@ def bqs():
     return m
 
 
-@pytest.mark.parametrize("level_loop", [0, 1])
-def test_bounded_wait_times_out_and_device_stays_usable(bqs, level_loop):
-    # level_loop 1: the levels enqueued after the failing one find no work.
+@pytest.mark.parametrize("level_loop,overlap", [(0, 0), (1, 0), (0, 1)])
+def test_bounded_wait_times_out_and_device_stays_usable(bqs, level_loop, overlap):
+    # level_loop 1: the levels enqueued after the failing one find no work; overlap 1:
+    # the call's stream still waits for the networks on the second stream.
     import torch
     a = inputs.make_keys(1 << 24, "int32", "uniform", seed=8)   # every block owns tiles
     t = torch.from_numpy(a).cuda()
     bqs.set_option("level_loop", level_loop)
+    bqs.set_option("overlap", overlap)
     old_limit = bqs.get_option("wait_limit")
     bqs.set_option("wait_limit", 1 << 16)      # give up after ~10 ms instead of seconds
     bqs.set_option("test_stall", 1)

@@ -365,3 +365,29 @@ def test_structured_distributions(bqs, dtype, dist, pivot):
     for n in (300_001, 1 << 20):
         a = inputs.make_keys(n, dtype, dist, seed=n)
         assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
+
+
+@pytest.mark.parametrize("small_sort", [0, 1])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_networks_on_a_second_stream(bqs, dtype, small_sort):
+    # BQS_OPT_OVERLAP: each level's networks run beside the partition levels.
+    import torch
+    bqs.set_option("overlap", 1)
+    bqs.set_option("small_sort", small_sort)
+    bqs.set_option("pivot", 1)
+    for n, dist in [(2049, "uniform"), (300_001, "mod_sqrt"), (1 << 22, "uniform"),
+                    (1 << 20, "swapped_1pct"), (100_000, "all_equal")]:
+        a = inputs.make_keys(n, dtype, dist, seed=n)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt"))
+        st = bqs.stats()
+        assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n
+    keys, vals = _pairs_case(dtype, 1 << 20, "dense", seed=4)
+    tk, tv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    bqs.sort_pairs(tk, tv)
+    wk, wv = oracle.sort_pairs(keys, vals)
+    assert_same_bits(tk.cpu().numpy(), wk)
+    assert_same_bits(tv.cpu().numpy().view(np.uint32), wv)
+    k2, off = inputs.make_segments(1000, seed=5, lo=1, hi=20_000, dtype=dtype)
+    t = torch.from_numpy(k2).cuda()
+    bqs.sort_segmented(t, torch.from_numpy(off).cuda())
+    assert_same_bits(t.cpu().numpy(), oracle.sort_segmented(k2, off))
