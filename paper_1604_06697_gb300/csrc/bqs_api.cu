@@ -96,16 +96,18 @@ void prepare_mempool() {
   done.push_back(dev);
 }
 
-Ctrl* pinned_ctrl() {
+Ctrl* pinned_ctrl(bool* mapped) {
   if (!t_pinned) {
     void* p = nullptr;
     if (cudaMallocHost(&p, sizeof(Ctrl)) != cudaSuccess) {
       cudaGetLastError();
       static thread_local Ctrl fallback;  // pageable: copies still complete on sync
+      *mapped = false;
       return &fallback;
     }
     t_pinned = (Ctrl*)p;
   }
+  *mapped = true;
   return t_pinned;
 }
 

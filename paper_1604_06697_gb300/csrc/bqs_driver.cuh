@@ -354,9 +354,26 @@ int capture_level_loop(const Params& P, const Variant& var, cudaStream_t s, int 
 // to kAhead levels enqueued and, before adding level j + kAhead, waits for level j's
 // flag (copied to pinned memory behind an event).  Levels enqueued past the last one
 // find empty lists and return at once.  Returns after the last level has run.
+// Copies the control block to the host.  Into pinned (device-mapped) memory a one-block
+// kernel writes it directly: a DMA copy would queue behind any large transfer the
+// caller has on the same copy engine (an upload or download overlapping the sort).
+static __global__ void k_ctrl_to_host(const Ctrl* __restrict__ c, Ctrl* h) {
+  static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(c);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(h);
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) dst[i] = src[i];
+}
+
+inline cudaError_t read_ctrl(const Ctrl* dev, Ctrl* host, bool mapped, cudaStream_t s) {
+  if (!mapped) return cudaMemcpyAsync(host, dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+  k_ctrl_to_host<<<1, 64, 0, s>>>(dev, host);
+  return cudaGetLastError();
+}
+
 template <class KT, bool PAIRS>
 int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_levels,
-                     bool local_on, bool timing, int test_stall, Ctrl* host, Stats& st) {
+                     bool local_on, bool timing, int test_stall, Ctrl* host, bool host_mapped,
+                     Stats& st) {
   constexpr int kAhead = 4;   // < 8, the size of the flag ring
   LevelRing& ring = level_ring();
   if (!ring.ok) return kErrNoMem;
@@ -393,7 +410,7 @@ int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_level
     more = (f & 1) != 0;
     ++checked;
   }
-  BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
   BQS_CK(cudaStreamSynchronize(s));
   if (host->status) return status_code(host->status);
   st.levels = (int64_t)host->levels_run;
@@ -499,7 +516,8 @@ int run_call(const Call& c, Stats& st) {
   if (!device_loop && !c.fixed_ws) helper_stream();   // created outside any capture
 
   static thread_local Ctrl pageable_ctrl;
-  Ctrl* host = (c.fixed_ws || device_loop) ? &pageable_ctrl : pinned_ctrl();
+  bool host_mapped = false;
+  Ctrl* host = (c.fixed_ws || device_loop) ? &pageable_ctrl : pinned_ctrl(&host_mapped);
   const bool timing = c.opt.timing && !c.fixed_ws && !device_loop;
   BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
 
@@ -531,7 +549,7 @@ int run_call(const Call& c, Stats& st) {
     P.device_loop = 1;
     P.p = 0;
     return run_levels_ahead<KT, PAIRS>(P, var, s, max_levels, local_cutoff > small_cutoff, timing,
-                                       c.opt.test_stall ? 1 : 0, host, st);
+                                       c.opt.test_stall ? 1 : 0, host, host_mapped, st);
   } else if (c.partition_only) {
     k_init_partition<KT><<<1, 32, 0, s>>>(P, c.n, c.pivot_raw);
     st.kernel_launches += 1;
@@ -542,7 +560,7 @@ int run_call(const Call& c, Stats& st) {
     k_init_segments<KT, PAIRS><<<g, 256, 0, s>>>(P, c.seg_offsets, c.nseg);
     st.kernel_launches += 1;
     BQS_CK(cudaGetLastError());
-    BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
     BQS_CK(cudaStreamSynchronize(s));
     if (host->status) return status_code(host->status);
     cur = host->lists[0];
@@ -668,7 +686,7 @@ int run_call(const Call& c, Stats& st) {
       // The next level's counts are final once bookkeeping and local partitioning have
       // run: read them back now, while this level's fills and sorting networks still
       // run, so the host enqueues the next level before the stream drains.
-      BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
       BQS_CK(cudaEventRecord(counts_ev, s));
     }
     if (nlarge) {
@@ -689,7 +707,7 @@ int run_call(const Call& c, Stats& st) {
     if (counts_ev) {
       BQS_CK(cudaEventSynchronize(counts_ev));
     } else {
-      BQS_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
       BQS_CK(cudaStreamSynchronize(s));
     }
     host_fresh = true;

@@ -67,7 +67,9 @@ int dispatch_call(int32_t dtype, const Call& c);   // runs c, keeps its statisti
 int64_t layout_bytes(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff);
 void user_workspace(void** ptr, int64_t* bytes);
 void prepare_mempool();
-Ctrl* pinned_ctrl();
+// The calling thread's control-block readback buffer: pinned host memory the device
+// can write (mapped = true), or pageable memory if pinning failed.
+Ctrl* pinned_ctrl(bool* mapped);
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();   // of the current device
 cudaEvent_t counts_event();     // the calling thread's, on the current device (null on failure)
 // The calling thread's second stream and its two events on the current device (null on
