@@ -196,7 +196,8 @@ typedef enum {
                                4 = median-of-3-medians-of-3; 5 = median-of-3-medians-
                                of-5; 6 = median-of-5-medians-of-5.  Samples are equally
                                spaced keys; every rule uses median-of-3 below 64 keys */
-  BQS_OPT_SMALL_CUTOFF = 1, /* small-segment cutoff C, 2 .. 2048 (default 2048) */
+  BQS_OPT_SMALL_CUTOFF = 1, /* small-segment cutoff C, 2 .. 4096 (default 2048); key-value
+                               sorts and BQS_OPT_SMALL_SORT = 1 use at most 2048 */
   BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
   BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */
   BQS_OPT_TILE = 4,         /* partition tile variant: 0 = default, 1..N autotuner choices */

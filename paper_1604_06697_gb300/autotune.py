@@ -20,7 +20,7 @@ import os
 from . import inputs
 
 TILES = (0, 1, 2, 3, 4, 5)     # TMA partition variants (see bqs_set_option(BQS_OPT_TILE))
-SMALL_CUTOFFS = (256, 1024, 2048)
+SMALL_CUTOFFS = (256, 1024, 2048, 4096)   # above 2048: key-only sorts, warp-group networks
 LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
 SMALL_SORTS = (0, 1)           # warp / warp-group networks, or 256-thread block networks
 OVERLAPS = (0, 1)              # networks on the call's stream, or beside the partitions
@@ -131,9 +131,12 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
+    # Cutoffs above 2048 keys exist only for key-only sorts with the warp-group networks
+    # (the library clamps the others to 2048): no duplicate candidates.
     cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o)
                            for t, s, l, w, o in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
-                                                                  SMALL_SORTS, OVERLAPS)]
+                                                                  SMALL_SORTS, OVERLAPS)
+                           if s <= 2048 or (kind != "pairs" and w == 0)]
     try:
         for cfg in cands:
             apply(cfg)

@@ -254,7 +254,7 @@ int bqs_set_option(int32_t opt, int64_t value) {
       g_opt.pivot_rule = value;
       return BQS_OK;
     case BQS_OPT_SMALL_CUTOFF:
-      if (value < 2 || value > kMaxSmall) return BQS_ERR_INVALID;
+      if (value < 2 || value > kMaxSmallKeys) return BQS_ERR_INVALID;
       g_opt.small_cutoff = value;
       return BQS_OK;
     case BQS_OPT_DEPTH_LIMIT:

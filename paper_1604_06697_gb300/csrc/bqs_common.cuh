@@ -95,6 +95,7 @@ struct ListCounts {
   unsigned int todo;    // large segments whose pivot k_pivot chooses
   unsigned int local;
   unsigned int group;   // small segments above the one-warp size (key-only sorts)
+  unsigned int big;     // small segments above kMaxSmall keys (key-only sorts)
 };
 
 struct Ctrl {
@@ -129,6 +130,7 @@ struct Lists {
   Run* small[2];
   Run* tiny[2];
   Run* group[2];
+  Run* big[2];
   uint32_t* todo[2];              // slots of large segments waiting for k_pivot
   Run* local[2];
   Fill* fill[2];
@@ -155,12 +157,12 @@ struct Params {
   // Network launches on a second stream take their list lengths from here (the
   // device-side counts of their lists may already be cleared for the next level).
   int fixed_counts;
-  uint32_t n_tiny, n_small, n_group;
+  uint32_t n_tiny, n_small, n_group, n_big;
 };
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {
   l->large = 0; l->fill = 0; l->large_keys = 0;
-  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0; l->group = 0;
+  l->small = 0; l->tiny = 0; l->todo = 0; l->local = 0; l->group = 0; l->big = 0;
 }
 
 // Parity of the lists the current level consumes: given by the host when it drives
@@ -183,7 +185,8 @@ constexpr int kStatusTimeout = -4;   // a bounded device-side wait gave up
 constexpr int kStatusOverflow = -6;  // an internal list overflowed its capacity
 
 constexpr int kFillTile = 8192;      // keys per fill task
-constexpr int kMaxSmall = 2048;      // largest small-segment cutoff
+constexpr int kMaxSmall = 2048;      // largest small-segment cutoff of key-value sorts
+constexpr int kMaxSmallKeys = 4096;  // largest small-segment cutoff of key-only sorts
 constexpr int kWarpSortMax = 256;    // small segments up to this length are sorted by one warp
 constexpr int kMaxSample = 511;      // largest pivot sample
 constexpr int kInlineFill = 32;      // pivot-class runs up to this length are written inline

@@ -25,7 +25,7 @@ namespace bqs {
 
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
-  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0};
+  size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0}, big[2] = {0, 0};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -34,10 +34,12 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Capacities: large segments are longer than the small cutoff and disjoint, so a level
 // holds at most n/(C+1) of them; each yields at most two children (or, at the first
-// level, one entry per caller segment).
+// level, one entry per caller segment).  Sized for C <= kMaxSmall, which holds for every
+// sort that the cutoff applies to (key-value sorts clamp C to kMaxSmall).
 inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff,
                           bool need_alt) {
   Layout L;
+  small_cutoff = std::min(small_cutoff, kMaxSmall);
   const uint64_t cap_large = (uint64_t)n / (uint64_t)(small_cutoff + 1) + 2;
   const uint64_t cap_run = std::max<uint64_t>(2 * cap_large, (uint64_t)nseg) + 2;
   L.cap_large = (uint32_t)std::min<uint64_t>(cap_large, 0xFFFFFFF0ull);
@@ -55,6 +57,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.cursor[i] = take((size_t)L.cap_large * 8);
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
     L.group[i] = take((size_t)L.cap_run * sizeof(Run));
+    L.big[i] = take((size_t)L.cap_run * sizeof(Run));
     L.tiny[i] = take((size_t)L.cap_run * sizeof(Run));
     L.todo[i] = take((size_t)L.cap_large * sizeof(uint32_t));
     L.local[i] = take((size_t)L.cap_run * sizeof(Run));
@@ -227,16 +230,17 @@ inline cudaStream_t helper_stream() {
 }
 
 // Launches the sorting networks of the `small` list (kWarpSortMax+1 .. group_min keys)
-// and of the `group` list (longer segments, key-only sorts with small_sort = 0).
-// Key-only sorts: one warp per `small` segment (k_small_warps) and one SmallGroup
-// block per `group` segment (k_small_group); key-value sorts, or small_sort = 1: one
-// 256-thread block per `small` segment (k_small_block), and `group` stays empty.
+// and of the `group` and `big` lists (longer segments, key-only sorts with
+// small_sort = 0).  Key-only sorts: one warp per `small` segment (k_small_warps), one
+// SmallGroup block per `group` segment (k_small_group) and per `big` segment
+// (k_small_big, cutoffs above kMaxSmall); key-value sorts, or small_sort = 1: one
+// 256-thread block per `small` segment (k_small_block), and `group` and `big` stay empty.
 // Counts are the list lengths when the host knows them (a launch is then skipped when
 // its list is empty); device_counts = true launches persistent grids that read them on
 // the device.  Returns the number of launches.
 template <class KT, bool PAIRS>
-int launch_small(const Params& P, int p, uint32_t small, uint32_t group, bool device_counts,
-                 cudaStream_t s) {
+int launch_small(const Params& P, int p, uint32_t small, uint32_t group, uint32_t big,
+                 bool device_counts, cudaStream_t s) {
   const int sms = sm_count();
   int n = 0;
   const bool warps = !PAIRS && P.small_sort == 0;
@@ -262,6 +266,11 @@ int launch_small(const Params& P, int p, uint32_t small, uint32_t group, bool de
       k_small_group<KT, PAIRS><<<(int)g, SmallGroup<KT>::T, 0, s>>>(P, p);
       ++n;
     }
+    if (warps && P.small_cutoff > kMaxSmall && (device_counts || big)) {
+      const uint32_t g = device_counts ? 8 * sms : std::min<uint32_t>(big, 8 * sms);
+      k_small_big<KT, PAIRS><<<(int)g, SmallGroup<KT>::TBIG, 0, s>>>(P, p);
+      ++n;
+    }
   }
   return n;
 }
@@ -282,7 +291,7 @@ void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, boo
   k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
   if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), s);
   k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
-  launch_small<KT, PAIRS>(P, 0, 0, 0, true, s);
+  launch_small<KT, PAIRS>(P, 0, 0, 0, 0, true, s);
 }
 
 // Pinned flags and events of the calling thread for the device-driven host loop.
@@ -400,7 +409,8 @@ int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_level
                              cudaMemcpyDeviceToHost, s));
       BQS_CK(cudaEventRecord(ring.ev[enq & 7], s));
       st.kernel_launches += (local_on ? 8 : 7) +
-                            ((!PAIRS && P.small_sort == 0 && P.small_cutoff > P.group_min) ? 2 : 1);
+                            ((!PAIRS && P.small_sort == 0 && P.small_cutoff > P.group_min) ? 2 : 1) +
+                            ((!PAIRS && P.small_sort == 0 && P.small_cutoff > kMaxSmall) ? 1 : 0);
       st.partition_launches += 1;
     }
     if (checked == enq) return kErrInternal;   // the device bounds the levels first
@@ -443,7 +453,10 @@ int run_call(const Call& c, Stats& st) {
   const auto& vars = variants<KT, PAIRS>();
   const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
   const int tile = var.threads * var.kpt;
-  const int small_cutoff = c.partition_only ? 1 : (int)c.opt.small_cutoff;
+  // Cutoffs above kMaxSmall apply to key-only sorts with the warp-group networks.
+  const int small_cutoff = c.partition_only ? 1
+                           : (PAIRS || c.opt.small_sort) ? (int)std::min<int64_t>(c.opt.small_cutoff, kMaxSmall)
+                                                         : (int)c.opt.small_cutoff;
   // Segments up to local_cutoff keys are partitioned down to the small-segment cutoff by
   // one thread block in shared memory (not below a cutoff of kWarpSortMax keys: the
   // block's sub-segment lists are sized for that).
@@ -482,6 +495,7 @@ int run_call(const Call& c, Stats& st) {
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
     P.l.group[i] = (Run*)(w + L.group[i]);
+    P.l.big[i] = (Run*)(w + L.big[i]);
     P.l.tiny[i] = (Run*)(w + L.tiny[i]);
     P.l.todo[i] = (uint32_t*)(w + L.todo[i]);
     P.l.local[i] = (Run*)(w + L.local[i]);
@@ -569,6 +583,7 @@ int run_call(const Call& c, Stats& st) {
     k_init_single<KT, PAIRS><<<1, 32, 0, s>>>(P, c.n);
     st.kernel_launches += 1;
     if (c.n <= small_cutoff && c.n <= kWarpSortMax) cur.tiny = 1;
+    else if (c.n <= small_cutoff && c.n > kMaxSmall) cur.big = 1;
     else if (c.n <= small_cutoff && c.n > P.group_min) cur.group = 1;
     else if (c.n <= small_cutoff) cur.small = 1;
     else if (c.n <= local_cutoff) cur.local = 1;
@@ -648,7 +663,7 @@ int run_call(const Call& c, Stats& st) {
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       if (side_work) BQS_CK(cudaStreamWaitEvent(s, done, 0));   // the previous level's networks
     }
-    if (s1 && (cur.tiny || cur.small || cur.group)) {
+    if (s1 && (cur.tiny || cur.small || cur.group || cur.big)) {
       // This level's networks, beside this and the next partition level.
       BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
       Params Q = P;
@@ -656,14 +671,15 @@ int run_call(const Call& c, Stats& st) {
       Q.n_tiny = cur.tiny;
       Q.n_small = cur.small;
       Q.n_group = cur.group;
+      Q.n_big = cur.big;
       if (cur.tiny) {
         st.small_segments += cur.tiny;
         k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s1>>>(Q, Q.p);
         st.kernel_launches += 1;
       }
-      if (cur.small || cur.group) {
-        st.small_segments += cur.small + cur.group;
-        st.kernel_launches += launch_small<KT, PAIRS>(Q, Q.p, cur.small, cur.group, false, s1);
+      if (cur.small || cur.group || cur.big) {
+        st.small_segments += cur.small + cur.group + cur.big;
+        st.kernel_launches += launch_small<KT, PAIRS>(Q, Q.p, cur.small, cur.group, cur.big, false, s1);
       }
       BQS_CK(cudaEventRecord(done, s1));
       side_work = true;
@@ -698,9 +714,9 @@ int run_call(const Call& c, Stats& st) {
       k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, s>>>(P, P.p);
       st.kernel_launches += 1;
     }
-    if (!s1 && (cur.small || cur.group)) {
-      st.small_segments += cur.small + cur.group;
-      st.kernel_launches += launch_small<KT, PAIRS>(P, P.p, cur.small, cur.group, false, s);
+    if (!s1 && (cur.small || cur.group || cur.big)) {
+      st.small_segments += cur.small + cur.group + cur.big;
+      st.kernel_launches += launch_small<KT, PAIRS>(P, P.p, cur.small, cur.group, cur.big, false, s);
     }
     BQS_CK(cudaGetLastError());
     if (!more) break;
@@ -732,7 +748,7 @@ int run_call(const Call& c, Stats& st) {
   } else if (!c.partition_only) {
     // A single array that went straight to a network or the single-block partitioning:
     // nothing was read back, and the counts follow from where it was routed.
-    st.small_keys = (cur.tiny | cur.small | cur.group) ? c.n : 0;
+    st.small_keys = (cur.tiny | cur.small | cur.group | cur.big) ? c.n : 0;
     st.local_keys = cur.local ? c.n : 0;
   }
   st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);

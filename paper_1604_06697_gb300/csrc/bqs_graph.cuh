@@ -28,7 +28,7 @@ static __global__ void k_level_end(Params P, cudaGraphConditionalHandle h, int m
     Ctrl* c = P.ctrl;
     const int q = (c->level & 1) ^ 1;
     const ListCounts& n = c->lists[q];
-    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group) != 0u;
+    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group | n.big) != 0u;
     if (c->status != 0) more = false;
     if (more && c->level + 1 > max_levels) {
       c->status = kStatusOverflow;
@@ -55,8 +55,8 @@ static __global__ void k_level_step(Params P, int max_levels) {
       c->active_total += cur.large_keys;
     }
     c->local_runs += cur.local;
-    c->small_runs += cur.small + cur.tiny + cur.group;
-    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group) != 0u;
+    c->small_runs += cur.small + cur.tiny + cur.group + cur.big;
+    bool more = ((unsigned)n.large | n.small | n.tiny | n.local | n.group | n.big) != 0u;
     if (c->status != 0) more = false;
     if (more && lvl + 1 > max_levels) {
       c->status = kStatusOverflow;

@@ -58,22 +58,27 @@ __device__ __forceinline__ bool lt(const Elem<KT, PAIRS>& a, const Elem<KT, PAIR
 
 // Median of three values (Sec. 2): the middle one of the ordered triple.
 template <class KT, bool PAIRS>
-__device__ Elem<KT, PAIRS> median3(Elem<KT, PAIRS> a, Elem<KT, PAIRS> b, Elem<KT, PAIRS> c) {
+__device__ __forceinline__ Elem<KT, PAIRS> median3(Elem<KT, PAIRS> a, Elem<KT, PAIRS> b, Elem<KT, PAIRS> c) {
   if (lt(b, a)) { auto t = a; a = b; b = t; }
   if (lt(c, b)) { auto t = b; b = c; c = t; }
   if (lt(b, a)) { auto t = a; a = b; b = t; }
   return b;
 }
 
-// Median of five values.
+// Ascending compare-exchange of two sample entries.
 template <class KT, bool PAIRS>
-__device__ Elem<KT, PAIRS> median5(Elem<KT, PAIRS>* e) {
-  for (int i = 1; i < 5; ++i) {        // insertion sort of five
-    Elem<KT, PAIRS> x = e[i];
-    int j = i;
-    while (j > 0 && lt(x, e[j - 1])) { e[j] = e[j - 1]; --j; }
-    e[j] = x;
-  }
+__device__ __forceinline__ void cx_elem(Elem<KT, PAIRS>& a, Elem<KT, PAIRS>& b) {
+  if (lt(b, a)) { const auto t = a; a = b; b = t; }
+}
+
+// Median of five values: the middle entry after a fixed 9-comparator sorting network
+// for five inputs (Knuth, TAOCP vol. 3, Sec. 5.3.4), so every index is a constant and
+// the five values stay in registers.
+template <class KT, bool PAIRS>
+__device__ __forceinline__ Elem<KT, PAIRS> median5(Elem<KT, PAIRS> (&e)[5]) {
+  cx_elem(e[0], e[1]); cx_elem(e[3], e[4]); cx_elem(e[2], e[4]);
+  cx_elem(e[2], e[3]); cx_elem(e[1], e[4]); cx_elem(e[0], e[3]);
+  cx_elem(e[0], e[2]); cx_elem(e[1], e[3]); cx_elem(e[1], e[2]);
   return e[2];
 }
 
@@ -109,13 +114,17 @@ template <class KT, bool PAIRS, int G, int K>
 __device__ Elem<KT, PAIRS> median_of_medians(const typename KT::U* keys, const uint32_t* vals,
                                              int64_t b, int64_t len) {
   Elem<KT, PAIRS> m[G];
+#pragma unroll
   for (int g = 0; g < G; ++g) {
     Elem<KT, PAIRS> e[K];
+#pragma unroll
     for (int j = 0; j < K; ++j)
       e[j] = load_elem<KT, PAIRS>(keys, vals, b + ((2 * (int64_t)(K * g + j) + 1) * len) / (2 * G * K));
-    m[g] = K == 3 ? median3<KT, PAIRS>(e[0], e[1], e[2]) : median5<KT, PAIRS>(e);
+    if constexpr (K == 3) m[g] = median3<KT, PAIRS>(e[0], e[1], e[2]);
+    else m[g] = median5<KT, PAIRS>(e);
   }
-  return G == 3 ? median3<KT, PAIRS>(m[0], m[1], m[2]) : median5<KT, PAIRS>(m);
+  if constexpr (G == 3) return median3<KT, PAIRS>(m[0], m[1], m[2]);
+  else return median5<KT, PAIRS>(m);
 }
 
 // A pivot one thread evaluates: every rule below 20000 keys, all but sqrt(n) above.
@@ -165,20 +174,23 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
   const bool has = active && len > 0;
   const bool sorted_now = has && len <= P.small_cutoff;
   const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
-  const bool group = sorted_now && len > P.group_min;    // one warp group per segment
-  const bool small = sorted_now && !tiny && !group;      // one warp or block per segment
+  const bool big = sorted_now && len > kMaxSmall;        // one larger warp group (key-only)
+  const bool group = sorted_now && !big && len > P.group_min;   // one warp group per segment
+  const bool small = sorted_now && !tiny && !group && !big;     // one warp or block per segment
   const bool local = has && !sorted_now && len <= P.local_cutoff;
   const bool large = has && !sorted_now && !local;
 
 #pragma unroll
-  for (int kind = 0; kind < 4; ++kind) {
-    const bool mine = kind == 0 ? tiny : kind == 1 ? small : kind == 2 ? local : group;
+  for (int kind = 0; kind < 5; ++kind) {
+    const bool mine = kind == 0 ? tiny : kind == 1 ? small : kind == 2 ? local : kind == 3 ? group : big;
     const unsigned m = __ballot_sync(~0u, mine);
     if (!m) continue;
     const int leader = __ffs(m) - 1;
     ListCounts& lc = c->lists[q];
-    unsigned int* counter = kind == 0 ? &lc.tiny : kind == 1 ? &lc.small : kind == 2 ? &lc.local : &lc.group;
-    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : kind == 2 ? P.l.local[q] : P.l.group[q];
+    unsigned int* counter = kind == 0 ? &lc.tiny : kind == 1 ? &lc.small : kind == 2 ? &lc.local
+                          : kind == 3 ? &lc.group : &lc.big;
+    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : kind == 2 ? P.l.local[q]
+              : kind == 3 ? P.l.group[q] : P.l.big[q];
     const unsigned keys = __reduce_add_sync(~0u, mine ? (unsigned)len : 0u);  // <= 32 * 2^14
     unsigned int base = 0;
     if (lane == leader) {

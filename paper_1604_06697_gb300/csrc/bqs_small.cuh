@@ -94,6 +94,7 @@ template <class KT>
 struct SmallGroup {   // the block that sorts segments above small_warp_max()
   static constexpr int RMAX = sizeof(typename KT::U) == 4 ? 32 : 16;   // keys per thread
   static constexpr int T = kMaxSmall / RMAX;
+  static constexpr int TBIG = kMaxSmallKeys / RMAX;   // the block for kMaxSmall+1 .. kMaxSmallKeys
 };
 
 template <class KT, int R, int T>
@@ -162,6 +163,21 @@ __global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<K
     if (r.len * 2 <= kMaxSmall) group_sort_run<KT, G::RMAX / 2, G::T>(P, r, threadIdx.x, s_x);
     else group_sort_run<KT, G::RMAX, G::T>(P, r, threadIdx.x, s_x);
   }
+}
+
+// Key-only small segments of kMaxSmall+1 .. kMaxSmallKeys keys (list `big`, small
+// cutoffs above kMaxSmall), one block of SmallGroup::TBIG threads each: the same network
+// with twice the threads, one more phase of exchanges between warps.
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(SmallGroup<KT>::TBIG, 65536 / (128 * SmallGroup<KT>::TBIG)) k_small_big(Params P, int p) {
+  using U = typename KT::U;
+  using G = SmallGroup<KT>;
+  static_assert(!PAIRS, "launched only for key-only sorts");
+  p = level_parity(P, p);
+  __shared__ __align__(16) U s_x[staging_entries<U, G::RMAX, G::TBIG>()];
+  const unsigned int count = min(P.fixed_counts ? P.n_big : P.ctrl->lists[p].big, P.l.cap_run);
+  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x)
+    group_sort_run<KT, G::RMAX, G::TBIG>(P, P.l.big[p][s], threadIdx.x, s_x);
 }
 
 // ---- key-value segments as packed 64-bit keys ------------------------------------------

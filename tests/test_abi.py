@@ -69,8 +69,12 @@ def test_options_round_trip(lib):
     try:
         bqs.set_option("small_cutoff", 64)
         assert bqs.get_option("small_cutoff") == 64
+        bqs.set_option("small_cutoff", 4096)       # key-only sorts; key-value clamp to 2048
+        assert bqs.get_option("small_cutoff") == 4096
         with pytest.raises(bqs.BqsError):
-            bqs.set_option("small_cutoff", 4096)
+            bqs.set_option("small_cutoff", 4097)
+        with pytest.raises(bqs.BqsError):
+            bqs.set_option("small_cutoff", 1)
         with pytest.raises(bqs.BqsError):
             bqs.set_option("pivot", 7)             # rules 0..6 (Sec. 4)
         old_pivot = bqs.get_option("pivot")

@@ -65,20 +65,22 @@ def test_levels_ahead_matches_oracle_and_host_loop(bqs, dtype, dist):
             assert_conservation(st, n)
 
 
+@pytest.mark.parametrize("cutoff", [2048, 4096])
 @pytest.mark.parametrize("tile", [0, 5])
 @pytest.mark.parametrize("local", [0, -1])
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_levels_ahead_options(bqs, dtype, local, tile):
+def test_levels_ahead_options(bqs, dtype, local, tile, cutoff):
     bqs.set_option("tile", tile)
     bqs.set_option("local_cutoff", local)
+    bqs.set_option("small_cutoff", cutoff)
     bqs.set_option("pivot", 1)
     for n, dist in [(300_001, "uniform"), (1 << 22, "mod_sqrt"), (100_000, "all_equal")]:
         a = inputs.make_keys(n, dtype, dist, seed=11)
         got, st = sort_with(bqs, a, 1)
         assert_same_bits(got, oracle.sort(a, pivot="sqrt"))
         assert_conservation(st, n)
-        if local != 0 and dist == "uniform":
-            assert st["local_keys"] > 0
+        if local != 0 and dist == "uniform" and (cutoff < 4096 or dtype == "int32"):
+            assert st["local_keys"] > 0     # one block holds 8192 32-bit or 4096 64-bit keys
 
 
 def test_levels_ahead_depth_fallback_and_timing(bqs):

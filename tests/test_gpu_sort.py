@@ -74,7 +74,7 @@ def test_sort_pivot_rules_and_tiles(bqs, dtype, tile, pivot):
         assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
 
 
-@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 1000, 2048])
+@pytest.mark.parametrize("cutoff", [2, 3, 16, 64, 1000, 2048, 3000, 4096])
 def test_small_cutoffs(bqs, cutoff):
     bqs.set_option("small_cutoff", cutoff)
     for dtype in DTYPES:
@@ -85,7 +85,7 @@ def test_small_cutoffs(bqs, cutoff):
 
 @pytest.mark.parametrize("pivot", [0, 1])
 @pytest.mark.parametrize("local", [-1, 0, 3000, 16384])
-@pytest.mark.parametrize("cutoff", [16, 256, 1000, 2048])
+@pytest.mark.parametrize("cutoff", [16, 256, 1000, 2048, 4096])
 def test_local_partition_cutoffs(bqs, cutoff, local, pivot):
     # Segments above the small cutoff and up to the local cutoff are partitioned down to
     # the small cutoff by one block in shared memory (for cutoffs of at least 256 keys);
@@ -101,7 +101,9 @@ def test_local_partition_cutoffs(bqs, cutoff, local, pivot):
             assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
             st = bqs.stats()
             assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n, (n, dist, st)
-            if local != 0 and cutoff >= 256 and n == 1 << 20:
+            block = 8192 if dtype == "int32" else 4096      # keys one block holds
+            reach = block if local in (-1, 16384) else local
+            if local != 0 and cutoff >= 256 and reach > cutoff and n == 1 << 20:
                 assert st["local_segments"] > 0
 
 
@@ -266,12 +268,15 @@ def test_sort_config1_median_of_3(bqs):
 @pytest.mark.parametrize("small_sort", [0, 1])
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_small_networks_every_length(bqs, dtype, small_sort):
-    # Segments of every length 1 .. 2048 (and again for 200 random lengths): each one
-    # goes straight to a network, warp (<= 256), warp (<= 512 / 1024), group or block.
+    # Segments of every length 1 .. C (and again for 200 random lengths): each one goes
+    # straight to a network, warp (<= 256), warp (<= 512 / 1024), group (<= 2048), the
+    # larger group (<= 4096, key-only warp-group networks) or block.
     import torch
     bqs.set_option("small_sort", small_sort)
-    rng = inputs.splitmix64(77, 200) % np.uint64(2048)
-    lens = list(range(1, 2049)) + [int(v) + 1 for v in rng]
+    top = 4096 if small_sort == 0 else 2048
+    bqs.set_option("small_cutoff", top)
+    rng = inputs.splitmix64(77, 200) % np.uint64(top)
+    lens = list(range(1, top + 1)) + [int(v) + 1 for v in rng]
     off = np.zeros(len(lens) + 1, np.int64)
     np.cumsum(lens, out=off[1:])
     for dist in ("uniform", "mod_sqrt", "reversed"):
@@ -284,7 +289,7 @@ def test_small_networks_every_length(bqs, dtype, small_sort):
 
 
 @pytest.mark.parametrize("small_sort", [0, 1])
-@pytest.mark.parametrize("cutoff", [300, 600, 1024, 1500, 2048])
+@pytest.mark.parametrize("cutoff", [300, 600, 1024, 1500, 2048, 2049, 4096])
 def test_small_networks_in_full_sorts(bqs, cutoff, small_sort):
     bqs.set_option("small_sort", small_sort)
     bqs.set_option("small_cutoff", cutoff)
@@ -326,7 +331,8 @@ def _pairs_case(dtype, n, kind, seed):
 def test_pairs_packed_and_fallback_networks(bqs, dtype, kind, small_sort):
     import torch
     bqs.set_option("small_sort", small_sort)
-    for cutoff, n in ((300, 200_003), (1024, 1 << 20), (2048, 777_777)):
+    # (a cutoff above 2048 is clamped to 2048 for key-value sorts)
+    for cutoff, n in ((300, 200_003), (1024, 1 << 20), (2048, 777_777), (4096, 300_007)):
         bqs.set_option("small_cutoff", cutoff)
         keys, vals = _pairs_case(dtype, n, kind, seed=cutoff)
         tk, tv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
@@ -367,13 +373,15 @@ def test_structured_distributions(bqs, dtype, dist, pivot):
         assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt" if pivot else "mo3"))
 
 
+@pytest.mark.parametrize("cutoff", [2048, 4096])
 @pytest.mark.parametrize("small_sort", [0, 1])
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_networks_on_a_second_stream(bqs, dtype, small_sort):
+def test_networks_on_a_second_stream(bqs, dtype, small_sort, cutoff):
     # BQS_OPT_OVERLAP: each level's networks run beside the partition levels.
     import torch
     bqs.set_option("overlap", 1)
     bqs.set_option("small_sort", small_sort)
+    bqs.set_option("small_cutoff", cutoff)
     bqs.set_option("pivot", 1)
     for n, dist in [(2049, "uniform"), (300_001, "mod_sqrt"), (1 << 22, "uniform"),
                     (1 << 20, "swapped_1pct"), (100_000, "all_equal")]:
