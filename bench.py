@@ -118,6 +118,42 @@ def replica_throughput(units_per_rank: float, ms_max: float, world: int) -> floa
 
 # ---- CPU oracle timing (bounded sample) --------------------------------------------------------
 
+def gpu_local_cpus(dev):
+    """CPUs of the NUMA node the GPU is attached to (sysfs), or None if unknown."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            text = f.read().strip()
+    except Exception:
+        return None
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus or None
+
+
+def pinned_near_gpu(dev, make):
+    """Allocates pinned host buffers (make()) from a thread bound to the GPU's own NUMA
+    node, so that their pages sit next to the GPU's host link; the affinity is restored
+    afterwards.  Returns (buffers, node CPUs used or None)."""
+    cpus = gpu_local_cpus(dev)
+    saved = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+    use = (cpus & saved) if (cpus and saved) else None
+    if use:
+        os.sched_setaffinity(0, use)
+    try:
+        return make(), (sorted(use) if use else None)
+    finally:
+        if use:
+            os.sched_setaffinity(0, saved)
+
+
 def time_oracle(a, seconds: float):
     """Sorts 2^24-key samples of the workload with the oracle until `seconds` have passed."""
     import oracle
@@ -380,8 +416,9 @@ def run_ours(a):
     e2e = None
     if not a.no_e2e:
         NB = 3
-        pin_in = torch.from_numpy(host).pin_memory()
-        pin_out = [torch.empty_like(pin_in).pin_memory() for _ in range(2)]
+        (pin_in, pin_out), near = pinned_near_gpu(
+            dev, lambda: (torch.from_numpy(host).pin_memory(),
+                          [torch.empty(host.shape, dtype=src.dtype).pin_memory() for _ in range(2)]))
         dbuf = [torch.empty_like(src) for _ in range(NB)]
         up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
@@ -432,7 +469,9 @@ def run_ours(a):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "pipelining": "triple-buffered: step k+1's pinned upload and step k-1's "
                              "download overlap step k's sort on two copy streams",
-               "result_check": bool((pin_out[(a.steps - 1) % 2][1:] >= pin_out[(a.steps - 1) % 2][:-1]).all())}
+               "result_check": bool((pin_out[(a.steps - 1) % 2][1:] >= pin_out[(a.steps - 1) % 2][:-1]).all()),
+               "host_buffers": ("pinned, allocated on the GPU's NUMA node (CPUs %d-%d)" % (near[0], near[-1])
+                                if near else "pinned (GPU's NUMA node unknown)")}
         del pin_in, pin_out, dbuf
 
     cpu = None

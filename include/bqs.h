@@ -227,12 +227,21 @@ typedef enum {
                                payload) where the segment's key range allows (always
                                for 32-bit keys), one 256-thread block otherwise;
                                1 = one 256-thread block per segment. */
-  BQS_OPT_OVERLAP = 10      /* 1: the sorting networks of each level run on a second
+  BQS_OPT_OVERLAP = 10,     /* 1: the sorting networks of each level run on a second
                                stream of the library's, beside the next partition
                                levels (they touch disjoint key ranges); the call's
                                stream waits for them before the call returns.  0 (the
                                default): everything on the caller's stream.  Used when
                                the host reads the counts after every level. */
+  BQS_OPT_LOCAL_SORT = 11   /* with BQS_OPT_LOCAL_CUTOFF on, key-only sorts and
+                               BQS_OPT_SMALL_SORT = 0: the block that partitions a
+                               segment in shared memory also sorts up to this many of
+                               its finished sub-segments there (the same warp-group
+                               networks), so the segment costs one HBM read and one
+                               write; further ones, and all with 0, go back to HBM for
+                               the network kernels.  0 .. 128, default 0 (measured
+                               slower: the block's load, partition and network phases
+                               run one after another at 2 blocks per SM) */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);

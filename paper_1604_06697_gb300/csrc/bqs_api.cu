@@ -293,6 +293,10 @@ int bqs_set_option(int32_t opt, int64_t value) {
       if (value < 0 || value > 1) return BQS_ERR_INVALID;
       g_opt.overlap = value;
       return BQS_OK;
+    case BQS_OPT_LOCAL_SORT:
+      if (value < 0 || value > kLocalSortCap) return BQS_ERR_INVALID;
+      g_opt.local_sort = value;
+      return BQS_OK;
     default:
       return BQS_ERR_UNSUPPORTED;
   }
@@ -313,6 +317,7 @@ int bqs_get_option(int32_t opt, int64_t* value) {
     case BQS_OPT_LEVEL_LOOP: *value = g_opt.level_loop; return BQS_OK;
     case BQS_OPT_SMALL_SORT: *value = g_opt.small_sort; return BQS_OK;
     case BQS_OPT_OVERLAP: *value = g_opt.overlap; return BQS_OK;
+    case BQS_OPT_LOCAL_SORT: *value = g_opt.local_sort; return BQS_OK;
     default: return BQS_ERR_UNSUPPORTED;
   }
 }

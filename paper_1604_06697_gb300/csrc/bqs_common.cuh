@@ -154,6 +154,8 @@ struct Params {
   int test_stall;       // failure-path test: one tile is never requested
   int small_sort;       // 0: warp / warp-group networks for key-only sorts; 1: 256-thread blocks
   int group_min;        // small segments longer than this go to the `group` list
+  int local_sort;       // > 0: the single-block local partitioning sorts up to this many
+                        // of a segment's leaves itself (at most kLocalSortCap)
   // Network launches on a second stream take their list lengths from here (the
   // device-side counts of their lists may already be cleared for the next level).
   int fixed_counts;

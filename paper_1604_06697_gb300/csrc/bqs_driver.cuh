@@ -151,15 +151,16 @@ const std::vector<Variant>& variants() {
 }
 
 // Shape of the single-block local partitioning: keys per block (L) and threads; both
-// ping-pong buffers of L keys (+ payloads) fit in shared memory.
-template <class KT, bool PAIRS>
+// ping-pong buffers of L keys (+ payloads) fit in shared memory.  SORT: the block also
+// sorts its finished sub-segments (key-only sorts).
+template <class KT, bool PAIRS, bool SORT = false>
 struct LocalCap {
   static constexpr int L = PAIRS ? 4096 : (int)(32768 / sizeof(typename KT::U));
   static constexpr int T = 256;
-  static constexpr size_t smem = LocalShape<KT, PAIRS, L>::smem;
+  static constexpr size_t smem = LocalShape<KT, PAIRS, L, T, SORT>::smem;
   static const void* fn() {
     static const void* f = [] {
-      const void* k = (const void*)k_local_partition<KT, PAIRS, L, T>;
+      const void* k = (const void*)k_local_partition<KT, PAIRS, L, T, SORT>;
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       return k;
     }();
@@ -168,7 +169,7 @@ struct LocalCap {
   static int grid();
   static void launch(const Params& P, int p, int grid, cudaStream_t st) {
     fn();
-    k_local_partition<KT, PAIRS, L, T><<<grid, T, smem, st>>>(P, p);
+    k_local_partition<KT, PAIRS, L, T, SORT><<<grid, T, smem, st>>>(P, p);
   }
 };
 
@@ -199,9 +200,27 @@ inline int sm_count() {
   return sms;
 }
 
-template <class KT, bool PAIRS>
-int LocalCap<KT, PAIRS>::grid() {
+template <class KT, bool PAIRS, bool SORT>
+int LocalCap<KT, PAIRS, SORT>::grid() {
   return persistent_grid(fn(), T, smem);
+}
+
+// Launches the single-block local partitioning over the `local` list of parity p:
+// `count` runs when the host knows it (0: a persistent grid that reads it on the
+// device); with P.local_sort the variant that sorts its finished sub-segments itself.
+template <class KT, bool PAIRS>
+void launch_local(const Params& P, int p, uint32_t count, cudaStream_t st) {
+  if constexpr (!PAIRS) {
+    if (P.local_sort) {
+      using C = LocalCap<KT, false, true>;
+      const int g = C::grid();
+      C::launch(P, p, count ? (int)std::min<uint32_t>(count, (uint32_t)g) : g, st);
+      return;
+    }
+  }
+  using C = LocalCap<KT, PAIRS, false>;
+  const int g = C::grid();
+  C::launch(P, p, count ? (int)std::min<uint32_t>(count, (uint32_t)g) : g, st);
 }
 
 // ---- the level loop --------------------------------------------------------------------------
@@ -289,7 +308,7 @@ void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, boo
   if (e1) cudaEventRecord(e1, s);
   k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P);
   k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
-  if (local_on) LocalCap<KT, PAIRS>::launch(P, 0, LocalCap<KT, PAIRS>::grid(), s);
+  if (local_on) launch_local<KT, PAIRS>(P, 0, 0, s);
   k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
   launch_small<KT, PAIRS>(P, 0, 0, 0, 0, true, s);
 }
@@ -511,6 +530,7 @@ int run_call(const Call& c, Stats& st) {
   P.wait_limit = (uint32_t)c.opt.wait_limit;
   P.test_stall = 0;
   P.small_sort = (int)c.opt.small_sort;
+  P.local_sort = (!PAIRS && P.small_sort == 0) ? (int)c.opt.local_sort : 0;
   // Small segments above one warp's capacity go to the `group` list (key-only sorts with
   // the warp networks); otherwise every small segment above kWarpSortMax is `small`.
   P.group_min = (!PAIRS && P.small_sort == 0) ? small_warp_max<KT, PAIRS>() : kMaxSmall;
@@ -598,7 +618,6 @@ int run_call(const Call& c, Stats& st) {
 
   const int sms = sm_count();
   const int part_grid_max = persistent_grid(var.fn, var.threads, var.smem);
-  const int local_grid = LocalCap<KT, PAIRS>::grid();
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
   size_t ev_used = 0;
 
@@ -693,7 +712,7 @@ int run_call(const Call& c, Stats& st) {
     }
     if (cur.local) {   // its finished sub-segments join the next level's network lists
       st.local_segments += cur.local;
-      LocalCap<KT, PAIRS>::launch(P, P.p, (int)std::min<uint32_t>(cur.local, (uint32_t)local_grid), s);
+      launch_local<KT, PAIRS>(P, P.p, cur.local, s);
       st.kernel_launches += 1;
     }
     const bool more = nlarge || cur.local;

@@ -32,6 +32,7 @@ struct Options {
   int64_t level_loop = 0;      // 1: the host enqueues levels ahead instead of reading counts
   int64_t small_sort = 0;      // 1: 256-thread block networks for every small segment
   int64_t overlap = 0;         // 1: sorting networks on a second stream, beside the partitions
+  int64_t local_sort = 0;      // leaves per segment the single-block local partitioning sorts
 };
 
 struct Call {

@@ -6,12 +6,14 @@
 // Sec. 3 to all of its unfinished sub-segments at once, ping-ponging between two
 // shared-memory buffers, until every sub-segment is short enough for a sorting network
 // (at most the small-segment cutoff).  After each level the pivot classes are written
-// to the final buffer (the pivot value, as everywhere), and the finished sub-segments
-// are written back to the segment's range in HBM and appended to the next level's
-// network lists.  The recursion is the same as on the global levels (the same pivot
-// rules, three-way split, pivot class excluded from both sides); only the levels
-// between L keys and the cutoff cost one HBM read and one write per key in total
-// instead of one of each per level.
+// to the final buffer (the pivot value, as everywhere).  The finished sub-segments
+// either are written back to the segment's range in HBM and appended to the next
+// level's network lists, or (SORT, key-only sorts) stay in shared memory and are
+// sorted there by the warp-group networks once the block's levels are done, straight
+// into the final buffer: the single-block sort of the segment (partition levels and
+// networks) then costs one HBM read and one write per key in total.  The recursion is
+// the same as on the global levels (the same pivot rules, three-way split, pivot class
+// excluded from both sides).
 #pragma once
 
 #include "bqs_small.cuh"
@@ -21,6 +23,8 @@ namespace bqs {
 constexpr int kLocalMaxAct = 64;    // active sub-segments per level (> L / kWarpSortMax)
 constexpr int kLocalMaxLeaf = 128;  // finished sub-segments per level (2 per active one)
 constexpr int kLocalChunk = 256;    // keys per warp work item (32 lanes x 8)
+constexpr int kLocalSortCap = 128;  // sub-segments one block sorts itself (SORT); more
+                                    // go back to HBM and the network kernels
 
 struct SubSeg {
   int begin;   // offset in the block's segment
@@ -29,21 +33,76 @@ struct SubSeg {
   int depth;   // partition levels above it
 };
 
-template <class KT, bool PAIRS, int L>
+// Shared memory: key buffers 0 and 1 (L keys each; with SORT buffer 1 also holds the
+// staging rows of the block's network groups), then payload buffers 0 and 1.
+template <class KT, bool PAIRS, int L, int T, bool SORT>
 struct LocalShape {
   using U = typename KT::U;
+  using G = SmallGroup<KT>;
+  static constexpr int kStageBig = (T / G::TBIG) * staging_entries<U, G::RMAX, G::TBIG>();
+  static constexpr int kStageSmall = (T / G::T) * staging_entries<U, G::RMAX, G::T>();
+  static constexpr int kEntries1 =
+      !SORT ? L : (L > kStageBig ? (L > kStageSmall ? L : kStageSmall)
+                                 : (kStageBig > kStageSmall ? kStageBig : kStageSmall));
   static constexpr size_t kbuf = (size_t)L * sizeof(U);
+  static constexpr size_t kbuf1 = (size_t)kEntries1 * sizeof(U);
   static constexpr size_t vbuf = PAIRS ? (size_t)L * 4 : 0;
-  static constexpr size_t smem = 2 * (kbuf + vbuf);
+  static constexpr size_t smem = kbuf + kbuf1 + 2 * vbuf;
 };
 
-template <class KT, bool PAIRS, int L, int T>
-__global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
+// The leaves one block sorts itself (SORT): first those above kMaxSmall keys, one
+// group of SmallGroup::TBIG threads each, then the others, one group of SmallGroup::T
+// threads each with the smallest of RMAX/4, RMAX/2, RMAX keys per thread that holds
+// the leaf.  Every leaf is in key buffer `kb0`; `stage` (key buffer 1) holds the
+// groups' staging rows.  Groups take leaves round-robin; every decision below is
+// uniform within a group, so its named barriers line up.
+template <class KT, int T>
+__device__ __forceinline__ void local_sort_leaves(const SubSeg* leaves, int nleaves,
+                                                  const typename KT::U* kb0,
+                                                  typename KT::U* stage, typename KT::U* fk,
+                                                  int tid) {
   using U = typename KT::U;
-  using S = LocalShape<KT, PAIRS, L>;
+  using G = SmallGroup<KT>;
+  {
+    constexpr int NG = T / G::TBIG;
+    const int g = tid / G::TBIG, gt = tid % G::TBIG;
+    U* sw = stage + g * staging_entries<U, G::RMAX, G::TBIG>();
+    for (int f = 0, k = 0; f < nleaves; ++f) {
+      const SubSeg a = leaves[f];
+      if (a.len <= kMaxSmall) continue;
+      if (k++ % NG != g) continue;
+      group_sort_keys<KT, G::RMAX, G::TBIG>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+    }
+  }
+  __syncthreads();   // the staging rows change owners
+  {
+    constexpr int NG = T / G::T;
+    const int g = tid / G::T, gt = tid % G::T;
+    U* sw = stage + g * staging_entries<U, G::RMAX, G::T>();
+    for (int f = 0, k = 0; f < nleaves; ++f) {
+      const SubSeg a = leaves[f];
+      if (a.len > kMaxSmall) continue;
+      if (k++ % NG != g) continue;
+      if (a.len <= (G::RMAX / 4) * G::T)
+        group_sort_keys<KT, G::RMAX / 4, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+      else if (a.len <= (G::RMAX / 2) * G::T)
+        group_sort_keys<KT, G::RMAX / 2, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+      else
+        group_sort_keys<KT, G::RMAX, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+    }
+  }
+}
+
+template <class KT, bool PAIRS, int L, int T, bool SORT>
+__global__ void __launch_bounds__(T, SORT ? 2 : 3) k_local_partition(Params P, int p) {
+  using U = typename KT::U;
+  using S = LocalShape<KT, PAIRS, L, T, SORT>;
   using E = Elem<KT, PAIRS>;
   constexpr int WARPS = T / 32;
   constexpr int KPL = kLocalChunk / 32;
+  constexpr int KPT = L / T;                   // keys per thread of the segment's load
+  static_assert(L % T == 0, "whole loads per thread");
+  static_assert(!(SORT && PAIRS), "the block's own networks are key-only");
   static_assert(L / (kWarpSortMax + 1) + 1 <= kLocalMaxAct, "active list capacity");
   static_assert(2 * kLocalMaxAct <= kLocalMaxLeaf, "leaf list capacity");
   static_assert(L < 65536, "packed per-sub-segment counts");
@@ -51,9 +110,9 @@ __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
   p = level_parity(P, p);
   const int q = p ^ 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  // buffer b: keys at smem + b*kbuf, payloads at smem + 2*kbuf + b*vbuf
+  // buffer b: keys at smem + b*kbuf, payloads at smem + kbuf + kbuf1 + b*vbuf
   auto kb = [&](int b) { return reinterpret_cast<U*>(smem + (size_t)b * S::kbuf); };
-  auto vb = [&](int b) { return reinterpret_cast<uint32_t*>(smem + 2 * S::kbuf + (size_t)b * S::vbuf); };
+  auto vb = [&](int b) { return reinterpret_cast<uint32_t*>(smem + S::kbuf + S::kbuf1 + (size_t)b * S::vbuf); };
   __shared__ SubSeg s_act[2][kLocalMaxAct];
   __shared__ U s_pk[kLocalMaxAct];            // pivot of each active sub-segment (raw bits)
   __shared__ uint32_t s_pv[kLocalMaxAct];
@@ -62,8 +121,11 @@ __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
   __shared__ SubSeg s_leaf[kLocalMaxLeaf];    // finished this level
   __shared__ int s_fill[kLocalMaxAct][2];     // pivot class: begin, length
   __shared__ int s_nact[2], s_nleaf;
+  __shared__ SubSeg s_done[SORT ? kLocalSortCap : 1];   // leaves this block sorts (SORT)
+  __shared__ int s_ndone;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cap = SORT ? min(P.local_sort, kLocalSortCap) : 0;   // leaves sorted here
   const unsigned int count = min(P.ctrl->lists[p].local, P.l.cap_run);
   U* fk = (U*)P.b.final_key;
   uint32_t* fv = P.b.final_val;
@@ -75,23 +137,59 @@ __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
     U* gk = (U*)P.b.key[X] + run.off;
     uint32_t* gv = PAIRS ? P.b.val[X] + run.off : nullptr;
     {
+      // All of a thread's loads are issued before its first shared-memory store.
       U* k0 = kb(0);
-      uint32_t* v0 = vb(0);
-      for (int i = tid; i < len; i += T) {
-        k0[i] = gk[i];
-        if constexpr (PAIRS) v0[i] = gv[i];
+      U kv[KPT];
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        const int e = i * T + tid;
+        kv[i] = e < len ? gk[e] : U(0);
+      }
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        const int e = i * T + tid;
+        if (e < len) k0[e] = kv[i];
+      }
+      if constexpr (PAIRS) {
+        uint32_t* v0 = vb(0);
+#pragma unroll
+        for (int i = 0; i < KPT; ++i) {
+          const int e = i * T + tid;
+          kv[i] = e < len ? (U)gv[e] : U(0);
+        }
+#pragma unroll
+        for (int i = 0; i < KPT; ++i) {
+          const int e = i * T + tid;
+          if (e < len) v0[e] = (uint32_t)kv[i];
+        }
       }
     }
     if (tid == 0) {
       s_nact[0] = 1;
       s_nact[1] = 0;
       s_act[0][0] = SubSeg{0, len, 0, run.pad};
+      s_ndone = 0;
     }
     __syncthreads();
 
     for (int cur = 0;; cur ^= 1) {
       const int nact = s_nact[cur];
-      if (nact == 0) break;
+      if (nact == 0) {
+        if constexpr (SORT) {
+          // Leaves in buffer 1 move to buffer 0, which then holds every leaf; buffer 1
+          // becomes the networks' staging rows.
+          const int nd = min(s_ndone, cap);
+          for (int f = warp; f < nd; f += WARPS) {
+            const SubSeg a = s_done[f];
+            if (a.buf == 1)
+              for (int i = lane; i < a.len; i += 32) kb(0)[a.begin + i] = kb(1)[a.begin + i];
+          }
+          __syncthreads();
+          local_sort_leaves<KT, T>(s_done, nd, kb(0), kb(1), fk + run.off, tid);
+          __syncthreads();   // shared memory is reused by the next run
+        }
+        break;
+      }
 
       // Pivots (the depth-limit fallback: midpoint of the ord-key range, then of the
       // payload range, as in k_pivot) and work-item starts.
@@ -228,9 +326,12 @@ __global__ void __launch_bounds__(T) k_local_partition(Params P, int p) {
                                 SubSeg{a.begin + a.len - ngt, ngt, a.buf ^ 1, a.depth + 1}};
         for (int c = 0; c < 2; ++c) {
           if (kids[c].len == 0) continue;
-          if (kids[c].len <= P.small_cutoff)
-            s_leaf[atomicAdd(&s_nleaf, 1)] = kids[c];
-          else
+          if (kids[c].len <= P.small_cutoff) {
+            int d = cap;
+            if constexpr (SORT) d = atomicAdd(&s_ndone, 1);
+            if (d < cap) s_done[d] = kids[c];                      // sorted here at the end
+            else s_leaf[atomicAdd(&s_nleaf, 1)] = kids[c];          // back to HBM
+          } else
             s_act[cur ^ 1][atomicAdd(&s_nact[cur ^ 1], 1)] = kids[c];
         }
       }

@@ -15,6 +15,22 @@
 
 namespace bqs {
 
+// Barrier of the T threads that run one network together.  A network whose group is
+// the whole block (the network kernels) uses the block barrier; several groups sharing
+// one block (the single-block local sort) each use their own named barrier, 1 + the
+// group's index (barrier 0 is __syncthreads), over T threads; a warp needs only
+// __syncwarp.
+template <int T>
+__device__ __forceinline__ void sync_group() {
+  static_assert(T % 32 == 0, "groups are whole warps");
+  if constexpr (T == 32) {
+    __syncwarp();
+  } else {
+    if (blockDim.x == T) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / T)), "n"(T) : "memory");
+  }
+}
+
 template <class U>
 __device__ __forceinline__ U shfl_xor_any(U x, int d) {
   if constexpr (sizeof(U) == 8) {
@@ -199,14 +215,14 @@ __device__ __forceinline__ void net_stage(U (&x)[R], uint32_t (&y)[R], int t, U*
     const bool keep_min = (t & d) == 0;
     swz_store_row<R>(s_x, t, x);
     if constexpr (PAIRS) swz_store_row<R>(s_y, t, y);
-    __syncthreads();
+    sync_group<T>();
     U p[R];
     uint32_t pv[R];
     swz_load_row<R>(s_x, t ^ d, p);
     if constexpr (PAIRS) swz_load_row<R>(s_y, t ^ d, pv);
 #pragma unroll
     for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
-    __syncthreads();
+    sync_group<T>();
   }
 }
 
@@ -299,12 +315,12 @@ __device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
         }
       } else {
         swz_store_row<R>(s_x, t, x);
-        __syncthreads();
+        sync_group<T>();
         U p[R];
         swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
         for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-        __syncthreads();
+        sync_group<T>();
       }
     }
     net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
@@ -364,12 +380,12 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
       const int d = j / R;
       const bool keep_min = (t & d) == 0;
       swz_store_row<R>(s_x, t, x);
-      __syncthreads();
+      sync_group<T>();
       uint32_t p[R];
       swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
       for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-      __syncthreads();
+      sync_group<T>();
     }
     if (j == R) {                                 // one lane stage: a shuffle
       const bool keep_min = (t & 1) == 0;
@@ -443,12 +459,12 @@ __device__ __forceinline__ void net_sort_transposed64(uint64_t (&x)[16], int t, 
       const int d = j / R;
       const bool keep_min = (t & d) == 0;
       swz_store_row<R>(s_x, t, x);
-      __syncthreads();
+      sync_group<T>();
       uint64_t p[R];
       swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
       for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-      __syncthreads();
+      sync_group<T>();
     }
     if (j == 16 * R) {                            // entry bit 8: the other half warp
       lane_stage(16);

@@ -97,15 +97,14 @@ struct SmallGroup {   // the block that sorts segments above small_warp_max()
   static constexpr int TBIG = kMaxSmallKeys / RMAX;   // the block for kMaxSmall+1 .. kMaxSmallKeys
 };
 
+// Sorts len <= R*T raw keys from src (global or shared memory) into dst (the final
+// buffer) with T threads; sw: their staging rows.
 template <class KT, int R, int T>
-__device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, int t,
-                                               typename KT::U* sw) {
+__device__ __forceinline__ void group_sort_keys(const typename KT::U* src, typename KT::U* dst,
+                                                int len, int t, typename KT::U* sw) {
   using U = typename KT::U;
   using S = RowSwizzle<U, R>;
-  const U* src = (const U*)P.b.key[r.parity] + r.off;
-  U* dst = (U*)P.b.final_key + r.off;
-  const int len = (int)r.len;
-  auto sync = [] { if constexpr (T == 32) __syncwarp(); else __syncthreads(); };
+  auto sync = [] { sync_group<T>(); };
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int e = i * T + t;
@@ -128,6 +127,14 @@ __device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, in
     if (e < len) dst[e] = KT::unord(sw[S::pos(e)]);
   }
   sync();
+}
+
+template <class KT, int R, int T>
+__device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, int t,
+                                               typename KT::U* sw) {
+  using U = typename KT::U;
+  group_sort_keys<KT, R, T>((const U*)P.b.key[r.parity] + r.off, (U*)P.b.final_key + r.off,
+                            (int)r.len, t, sw);
 }
 
 // Key-only small segments of kWarpSortMax+1 .. small_warp_max() keys (list `small`),

@@ -82,6 +82,14 @@ def test_options_round_trip(lib):
             bqs.set_option("pivot", rule)
             assert bqs.get_option("pivot") == rule
         bqs.set_option("pivot", old_pivot)
+        old_ls = bqs.get_option("local_sort")
+        assert old_ls == 0                          # default: leaves go to the network kernels
+        for v in (0, 1, 128):
+            bqs.set_option("local_sort", v)
+            assert bqs.get_option("local_sort") == v
+        with pytest.raises(bqs.BqsError):
+            bqs.set_option("local_sort", 129)
+        bqs.set_option("local_sort", old_ls)
     finally:
         bqs.set_option("small_cutoff", old)
 

@@ -1,0 +1,24 @@
+"""Host-side helpers of bench.py that need no GPU."""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+@pytest.mark.skipif(not hasattr(os, "sched_getaffinity"), reason="no CPU affinity API")
+def test_pinned_buffers_bind_to_the_gpu_node_and_restore_affinity(monkeypatch):
+    before = os.sched_getaffinity(0)
+    node = {min(before)}                      # pretend the GPU's node holds one CPU
+    monkeypatch.setattr(bench, "gpu_local_cpus", lambda dev: node)
+    seen = []
+    out, used = bench.pinned_near_gpu(0, lambda: seen.append(os.sched_getaffinity(0)) or "buf")
+    assert out == "buf" and seen == [node] and used == sorted(node)
+    assert os.sched_getaffinity(0) == before
+    # unknown node: nothing changes
+    monkeypatch.setattr(bench, "gpu_local_cpus", lambda dev: None)
+    seen.clear()
+    out, used = bench.pinned_near_gpu(0, lambda: seen.append(os.sched_getaffinity(0)) or "buf")
+    assert used is None and seen == [before] and os.sched_getaffinity(0) == before

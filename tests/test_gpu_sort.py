@@ -107,6 +107,26 @@ def test_local_partition_cutoffs(bqs, cutoff, local, pivot):
                 assert st["local_segments"] > 0
 
 
+@pytest.mark.parametrize("local_sort", [0, 1, 128])
+@pytest.mark.parametrize("cutoff", [256, 2048, 4096])
+def test_local_sort_of_the_leaves(bqs, cutoff, local_sort):
+    # The single-block local partitioning sorts up to `local_sort` finished
+    # sub-segments of its segment in shared memory; the others (all with 0) go back to
+    # HBM for the network kernels.  1 sends almost every leaf down the second path
+    # while the block sorts one, so both paths share every segment.
+    bqs.set_option("small_cutoff", cutoff)
+    bqs.set_option("local_cutoff", -1)
+    bqs.set_option("local_sort", local_sort)
+    bqs.set_option("pivot", 1)
+    for dtype in DTYPES:
+        for n, dist in [(8192, "uniform"), (8193, "reversed"), (300_001, "mod_sqrt"),
+                        (1 << 20, "uniform"), (1 << 20, "swapped_1pct"), (77_777, "all_equal")]:
+            a = inputs.make_keys(n, dtype, dist, seed=n + cutoff + local_sort)
+            assert_same_bits(gpu_sort(bqs, a), oracle.sort(a, pivot="sqrt"))
+            st = bqs.stats()
+            assert st["equal_keys"] + st["small_keys"] + st["local_keys"] == n, (n, dist, st)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_local_partition_depth_fallback_and_pairs(bqs, dtype):
     import torch
