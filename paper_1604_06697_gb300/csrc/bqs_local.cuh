@@ -71,7 +71,7 @@ __device__ __forceinline__ void local_sort_leaves(const SubSeg* leaves, int nlea
       const SubSeg a = leaves[f];
       if (a.len <= kMaxSmall) continue;
       if (k++ % NG != g) continue;
-      group_sort_keys<KT, G::RMAX, G::TBIG>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+      group_sort_keys<KT, G::RMAX, G::TBIG, true>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
     }
   }
   __syncthreads();   // the staging rows change owners
@@ -84,11 +84,11 @@ __device__ __forceinline__ void local_sort_leaves(const SubSeg* leaves, int nlea
       if (a.len > kMaxSmall) continue;
       if (k++ % NG != g) continue;
       if (a.len <= (G::RMAX / 4) * G::T)
-        group_sort_keys<KT, G::RMAX / 4, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+        group_sort_keys<KT, G::RMAX / 4, G::T, true>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
       else if (a.len <= (G::RMAX / 2) * G::T)
-        group_sort_keys<KT, G::RMAX / 2, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+        group_sort_keys<KT, G::RMAX / 2, G::T, true>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
       else
-        group_sort_keys<KT, G::RMAX, G::T>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+        group_sort_keys<KT, G::RMAX, G::T, true>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
     }
   }
 }

@@ -16,18 +16,21 @@
 namespace bqs {
 
 // Barrier of the T threads that run one network together.  A network whose group is
-// the whole block (the network kernels) uses the block barrier; several groups sharing
-// one block (the single-block local sort) each use their own named barrier, 1 + the
-// group's index (barrier 0 is __syncthreads), over T threads; a warp needs only
-// __syncwarp.
-template <int T>
+// the whole block (the network kernels) uses the block barrier; with NB several groups
+// share one block (the single-block local sort) and each uses its own named barrier,
+// 1 + the group's index (barrier 0 is __syncthreads), over T threads.  NB is a
+// template flag because a kernel that may name a barrier by a register is given all
+// 16 of the block's barriers, which lowers how many of its blocks fit on an SM.  A
+// warp needs only __syncwarp.
+template <int T, bool NB = false>
 __device__ __forceinline__ void sync_group() {
   static_assert(T % 32 == 0, "groups are whole warps");
   if constexpr (T == 32) {
     __syncwarp();
+  } else if constexpr (!NB) {
+    __syncthreads();
   } else {
-    if (blockDim.x == T) __syncthreads();
-    else asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / T)), "n"(T) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / T)), "n"(T) : "memory");
   }
 }
 
@@ -215,14 +218,14 @@ __device__ __forceinline__ void net_stage(U (&x)[R], uint32_t (&y)[R], int t, U*
     const bool keep_min = (t & d) == 0;
     swz_store_row<R>(s_x, t, x);
     if constexpr (PAIRS) swz_store_row<R>(s_y, t, y);
-    sync_group<T>();
+    __syncthreads();
     U p[R];
     uint32_t pv[R];
     swz_load_row<R>(s_x, t ^ d, p);
     if constexpr (PAIRS) swz_load_row<R>(s_y, t ^ d, pv);
 #pragma unroll
     for (int i = 0; i < R; ++i) keep_one<PAIRS>(x[i], y[i], p[i], PAIRS ? pv[i] : 0u, keep_min);
-    sync_group<T>();
+    __syncthreads();
   }
 }
 
@@ -291,7 +294,7 @@ __device__ __forceinline__ void net_sort(U (&x)[R], uint32_t (&y)[R], int t, U* 
 // stages, whose code is shared by all phases.  The fully unrolled network for R = 32
 // is tens of thousands of instructions and stalls on instruction fetch; this form
 // keeps one phase body.  Key-only.
-template <int R, int T, class U>
+template <int R, int T, class U, bool NB = false>
 __device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
   constexpr int M = R * T;
   uint32_t none[R];   // payload slots of the shared stage code: never read (key-only)
@@ -315,12 +318,12 @@ __device__ __forceinline__ void net_sort_looped(U (&x)[R], int t, U* s_x) {
         }
       } else {
         swz_store_row<R>(s_x, t, x);
-        sync_group<T>();
+        sync_group<T, NB>();
         U p[R];
         swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
         for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-        sync_group<T>();
+        sync_group<T, NB>();
       }
     }
     net_merge<false, R, T, R / 2>(x, none, t, s_x, (uint32_t*)nullptr);
@@ -362,7 +365,7 @@ __device__ __forceinline__ void transposed_stages(uint32_t (&x)[32], int nb) {
   }
 }
 
-template <int T>
+template <int T, bool NB = false>
 __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, uint32_t* s_x) {
   constexpr int R = 32, M = R * T;
   uint32_t none[R];
@@ -380,12 +383,12 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
       const int d = j / R;
       const bool keep_min = (t & d) == 0;
       swz_store_row<R>(s_x, t, x);
-      sync_group<T>();
+      sync_group<T, NB>();
       uint32_t p[R];
       swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
       for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-      sync_group<T>();
+      sync_group<T, NB>();
     }
     if (j == R) {                                 // one lane stage: a shuffle
       const bool keep_min = (t & 1) == 0;
@@ -433,7 +436,7 @@ __device__ __forceinline__ void transposed_stages16(uint64_t (&x)[16], int nb) {
   }
 }
 
-template <int T>
+template <int T, bool NB = false>
 __device__ __forceinline__ void net_sort_transposed64(uint64_t (&x)[16], int t, uint64_t* s_x) {
   constexpr int R = 16, M = R * T;
   uint32_t none[R];
@@ -459,12 +462,12 @@ __device__ __forceinline__ void net_sort_transposed64(uint64_t (&x)[16], int t, 
       const int d = j / R;
       const bool keep_min = (t & d) == 0;
       swz_store_row<R>(s_x, t, x);
-      sync_group<T>();
+      sync_group<T, NB>();
       uint64_t p[R];
       swz_load_row<R>(s_x, t ^ d, p);
 #pragma unroll
       for (int i = 0; i < R; ++i) x[i] = keep_min ? umin_(x[i], p[i]) : umax_(x[i], p[i]);
-      sync_group<T>();
+      sync_group<T, NB>();
     }
     if (j == 16 * R) {                            // entry bit 8: the other half warp
       lane_stage(16);

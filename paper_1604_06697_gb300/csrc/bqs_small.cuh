@@ -98,13 +98,14 @@ struct SmallGroup {   // the block that sorts segments above small_warp_max()
 };
 
 // Sorts len <= R*T raw keys from src (global or shared memory) into dst (the final
-// buffer) with T threads; sw: their staging rows.
-template <class KT, int R, int T>
+// buffer) with T threads; sw: their staging rows.  NB: the T threads are one of several
+// groups of the block (named barriers).
+template <class KT, int R, int T, bool NB = false>
 __device__ __forceinline__ void group_sort_keys(const typename KT::U* src, typename KT::U* dst,
                                                 int len, int t, typename KT::U* sw) {
   using U = typename KT::U;
   using S = RowSwizzle<U, R>;
-  auto sync = [] { sync_group<T>(); };
+  auto sync = [] { sync_group<T, NB>(); };
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int e = i * T + t;
@@ -116,9 +117,9 @@ __device__ __forceinline__ void group_sort_keys(const typename KT::U* src, typen
   swz_load_row<R>(sw, t, x);
   // Exchanges between warps (T > 32) store a thread's own row before a barrier and
   // read another's after it, so the staging array doubles as their scratch.
-  if constexpr (sizeof(U) == 4 && R == 32) net_sort_transposed<T>(x, t, sw);
-  else if constexpr (sizeof(U) == 8 && R == 16) net_sort_transposed64<T>(x, t, sw);
-  else net_sort_looped<R, T>(x, t, sw);
+  if constexpr (sizeof(U) == 4 && R == 32) net_sort_transposed<T, NB>(x, t, sw);
+  else if constexpr (sizeof(U) == 8 && R == 16) net_sort_transposed64<T, NB>(x, t, sw);
+  else net_sort_looped<R, T, U, NB>(x, t, sw);
   swz_store_row<R>(sw, t, x);
   sync();
 #pragma unroll
