@@ -291,33 +291,6 @@ __global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* 
   }
 }
 
-// ---- shared-memory sorting network --------------------------------------------------------
-
-// Bitonic sort (Batcher) of m = power-of-two (ord key, payload) entries in shared
-// memory, ascending, by all threads of the block.  Ends with a barrier.
-template <bool PAIRS, class U>
-__device__ void block_bitonic_sort(U* k, uint32_t* v, int m) {
-  for (int size = 2; size <= m; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < (m >> 1); i += blockDim.x) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        U a = k[lo], b = k[hi];
-        uint32_t va = 0, vb = 0;
-        if constexpr (PAIRS) { va = v[lo]; vb = v[hi]; }
-        const bool swap = up ? elem_less<PAIRS>(b, vb, a, va) : elem_less<PAIRS>(a, va, b, vb);
-        if (swap) {
-          k[lo] = b; k[hi] = a;
-          if constexpr (PAIRS) { v[lo] = vb; v[hi] = va; }
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
-
 // ---- pivot selection kernel ---------------------------------------------------------------
 
 // Pivots that need more than one thread (the list `todo`):
@@ -332,8 +305,9 @@ template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_pivot(Params P) {
   using U = typename KT::U;
   using E = Elem<KT, PAIRS>;
-  __shared__ U s_k[kMaxSample + 1];
-  __shared__ uint32_t s_v[PAIRS ? kMaxSample + 1 : 1];
+  static_assert(kMaxSample < 512, "two sample entries per thread of 256");
+  __shared__ __align__(16) U s_k[512];                   // staging rows of the sample sort
+  __shared__ __align__(16) uint32_t s_v[PAIRS ? 512 : 1];
   __shared__ U s_red[2][8];
   __shared__ uint32_t s_redv[2][8];
 
@@ -442,28 +416,34 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
         piv.v = vmin + (vmax - vmin) / 2;
       }
       if (threadIdx.x == 0) atomicAdd(&P.ctrl->fallbacks, 1ull);
+      if (threadIdx.x == 0) {
+        segs[s].pkey = (uint64_t)KT::unord(piv.k);
+        segs[s].pval = piv.v;
+      }
     } else {
+      // 257 .. kMaxSample samples: 512 entries, two per thread in registers, sorted by
+      // the block's bitonic network (stages between warps through s_k / s_v).
       const int64_t k = sample_size(len);
-      const int m = next_pow2((int)k);
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        if (i < k) {
-          const int64_t pos = b + ((2 * (int64_t)i + 1) * len) / (2 * k);
-          s_k[i] = KT::ord(keys[pos]);
-          if constexpr (PAIRS) s_v[i] = vals[pos];
+      U x[2];
+      uint32_t y[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int e = (int)threadIdx.x * 2 + i;
+        if (e < k) {
+          const int64_t pos = b + ((2 * (int64_t)e + 1) * len) / (2 * k);
+          x[i] = KT::ord(keys[pos]);
+          y[i] = PAIRS ? vals[pos] : 0u;
         } else {
-          s_k[i] = ~U(0);
-          if constexpr (PAIRS) s_v[i] = 0xFFFFFFFFu;
+          x[i] = ~U(0);
+          y[i] = 0xFFFFFFFFu;
         }
       }
-      block_bitonic_sort<PAIRS>(s_k, s_v, m);
-      if (threadIdx.x == 0) {
-        piv.k = s_k[(k - 1) / 2];
-        piv.v = PAIRS ? s_v[(k - 1) / 2] : 0u;
+      net_sort<PAIRS, 2, 256>(x, y, (int)threadIdx.x, s_k, s_v);
+      const int med = (int)((k - 1) / 2);
+      if ((int)threadIdx.x == med / 2) {
+        segs[s].pkey = (uint64_t)KT::unord(x[med & 1]);
+        segs[s].pval = PAIRS ? y[med & 1] : 0u;
       }
-    }
-    if (threadIdx.x == 0) {
-      segs[s].pkey = (uint64_t)KT::unord(piv.k);
-      segs[s].pval = piv.v;
     }
     __syncthreads();
   }
