@@ -95,6 +95,10 @@ struct SmallGroup {   // the block that sorts segments above small_warp_max()
   static constexpr int RMAX = sizeof(typename KT::U) == 4 ? 32 : 16;   // keys per thread
   static constexpr int T = kMaxSmall / RMAX;
   static constexpr int TBIG = kMaxSmallKeys / RMAX;   // the block for kMaxSmall+1 .. kMaxSmallKeys
+  // Resident blocks per SM asked of the compiler: 24 warps per SM, the most whose
+  // register budget (72-78 per thread) the networks fit without spilling.
+  static constexpr int BLOCKS = 24 * 32 / T;
+  static constexpr int BLOCKS_BIG = 24 * 32 / TBIG;
 };
 
 // Sorts len <= R*T raw keys from src (global or shared memory) into dst (the final
@@ -139,9 +143,10 @@ __device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, in
 }
 
 // Key-only small segments of kWarpSortMax+1 .. small_warp_max() keys (list `small`),
-// one warp each.
+// one warp each; 5 blocks per SM for 32-bit keys (96 registers), 4 for 64-bit ones
+// (the most without spilling).
 template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
+__global__ void __launch_bounds__(128, sizeof(typename KT::U) == 4 ? 5 : 4) k_small_warps(Params P, int p) {
   using U = typename KT::U;
   constexpr int kMax = small_warp_max<KT, PAIRS>();
   static_assert(kMax >= 512, "launched only for key-only sorts");
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(128, 4) k_small_warps(Params P, int p) {
 // Key-only small segments above small_warp_max() (list `group`), one group of
 // SmallGroup::T threads (the whole block) each.
 template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<KT>::T)) k_small_group(Params P, int p) {
+__global__ void __launch_bounds__(SmallGroup<KT>::T, SmallGroup<KT>::BLOCKS) k_small_group(Params P, int p) {
   using U = typename KT::U;
   using G = SmallGroup<KT>;
   static_assert(!PAIRS, "launched only for key-only sorts");
@@ -177,7 +182,7 @@ __global__ void __launch_bounds__(SmallGroup<KT>::T, 65536 / (128 * SmallGroup<K
 // cutoffs above kMaxSmall), one block of SmallGroup::TBIG threads each: the same network
 // with twice the threads, one more phase of exchanges between warps.
 template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(SmallGroup<KT>::TBIG, 65536 / (128 * SmallGroup<KT>::TBIG)) k_small_big(Params P, int p) {
+__global__ void __launch_bounds__(SmallGroup<KT>::TBIG, SmallGroup<KT>::BLOCKS_BIG) k_small_big(Params P, int p) {
   using U = typename KT::U;
   using G = SmallGroup<KT>;
   static_assert(!PAIRS, "launched only for key-only sorts");
