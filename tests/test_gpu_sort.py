@@ -148,6 +148,18 @@ def test_local_partition_depth_fallback_and_pairs(bqs, dtype):
     assert bqs.stats()["local_segments"] > 0
 
 
+def test_pivot_kernel_with_many_block_pivots(bqs):
+    # Depth limit 0 sends every large segment to the pivot kernel's block phase; with
+    # cutoff 2 a level holds far more of them than a block's list takes (64 per block),
+    # so the blocks fall back to reading their entries again.
+    bqs.set_option("depth_limit", 0)
+    bqs.set_option("small_cutoff", 2)
+    for dtype in DTYPES:
+        a = inputs.make_keys(1 << 20, dtype, "uniform", seed=9)
+        assert_same_bits(gpu_sort(bqs, a), oracle.sort(a))
+        assert bqs.stats()["fallback_pivots"] > 64 * 8 * 152
+
+
 def test_float64_special_values(bqs):
     vals = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, 5e-324, -5e-324, 2.5, -2.5,
                      np.finfo(np.float64).max, -np.finfo(np.float64).max] * 500)
