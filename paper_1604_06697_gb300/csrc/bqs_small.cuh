@@ -95,10 +95,14 @@ struct SmallGroup {   // the block that sorts segments above small_warp_max()
   static constexpr int RMAX = sizeof(typename KT::U) == 4 ? 32 : 16;   // keys per thread
   static constexpr int T = kMaxSmall / RMAX;
   static constexpr int TBIG = kMaxSmallKeys / RMAX;   // the block for kMaxSmall+1 .. kMaxSmallKeys
-  // Resident blocks per SM asked of the compiler: 24 warps per SM, the most whose
-  // register budget (72-78 per thread) the networks fit without spilling.
-  static constexpr int BLOCKS = 24 * 32 / T;
-  static constexpr int BLOCKS_BIG = 24 * 32 / TBIG;
+  // Resident blocks per SM asked of the compiler.  32-bit keys: 24 warps per SM, the
+  // most whose register budget (76-78 per thread) the networks fit without spilling
+  // (2^28 int32 sort with cutoff 4096: 9.81 against 9.93 ms at 16 warps).  64-bit
+  // keys: 16 warps (128 registers); 24 warps (72 registers) measured slower (20.53
+  // against 20.15 ms at 2^28).
+  static constexpr bool k32 = sizeof(typename KT::U) == 4;
+  static constexpr int BLOCKS = (k32 ? 24 : 16) * 32 / T;
+  static constexpr int BLOCKS_BIG = (k32 ? 24 : 16) * 32 / TBIG;
 };
 
 // Sorts len <= R*T raw keys from src (global or shared memory) into dst (the final
