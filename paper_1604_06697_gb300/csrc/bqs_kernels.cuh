@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* 
 // Pivots that need more than one thread (the list `todo`):
 //  * sqrt rule (Sec. 4) at 20000 keys and more: the median of k = floor(sqrt(len))|1
 //    equally spaced keys (k capped at kMaxSample); samples of up to 256 keys are
-//    sorted in registers by one warp each, larger ones in shared memory by one block;
+//    sorted in registers by one warp each, larger ones by the whole block (two
+//    entries per thread in registers, stages between warps through shared memory);
 //  * a segment at the depth limit gets the midpoint of its ord-key range (payload
 //    range when all its keys are equal): each such level halves the range, so the
 //    recursion depth stays bounded by the key width (the role Heapsort plays in Sec. 2).
