@@ -75,6 +75,16 @@ def _time(run, reps: int) -> float:
     return min(ms)
 
 
+def candidate_configs(kind: str = "sort") -> list:
+    """Every launch shape the tuner times for a workload kind.  Cutoffs above 2048 keys
+    exist only for key-only sorts with the warp-group networks (the library clamps the
+    others to 2048), so they are not timed twice."""
+    return [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o)
+            for t, s, l, w, o in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
+                                                   SMALL_SORTS, OVERLAPS)
+            if s <= 2048 or (kind != "pairs" and w == 0)]
+
+
 def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
          cache_path: str | None = None, force: bool = False, candidates=None) -> dict:
     """Returns (and caches) the fastest configuration for this workload class.
@@ -131,12 +141,7 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
-    # Cutoffs above 2048 keys exist only for key-only sorts with the warp-group networks
-    # (the library clamps the others to 2048): no duplicate candidates.
-    cands = candidates or [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o)
-                           for t, s, l, w, o in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
-                                                                  SMALL_SORTS, OVERLAPS)
-                           if s <= 2048 or (kind != "pairs" and w == 0)]
+    cands = candidates or candidate_configs(kind)
     try:
         for cfg in cands:
             apply(cfg)

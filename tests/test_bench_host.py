@@ -22,3 +22,19 @@ def test_pinned_buffers_bind_to_the_gpu_node_and_restore_affinity(monkeypatch):
     seen.clear()
     out, used = bench.pinned_near_gpu(0, lambda: seen.append(os.sched_getaffinity(0)) or "buf")
     assert used is None and seen == [before] and os.sched_getaffinity(0) == before
+
+
+def test_autotune_candidates_cover_every_knob_once():
+    from paper_1604_06697_gb300 import autotune
+    for kind in ("sort", "pairs", "batched"):
+        cands = autotune.candidate_configs(kind)
+        keys = [tuple(sorted(c.items())) for c in cands]
+        assert len(keys) == len(set(keys))                       # no duplicates
+        assert all(set(c) == set(autotune.KNOBS) for c in cands)
+        for c in cands:                                          # 4096 only where it applies
+            if c["small_cutoff"] > 2048:
+                assert kind != "pairs" and c["small_sort"] == 0
+        big = [c for c in cands if c["small_cutoff"] > 2048]
+        per_cutoff = len(autotune.TILES) * len(autotune.LOCAL_CUTOFFS) * len(autotune.OVERLAPS)
+        assert len(big) == (0 if kind == "pairs" else per_cutoff)
+        assert len(cands) - len(big) == per_cutoff * len(autotune.SMALL_SORTS) * 3
