@@ -311,6 +311,9 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   __shared__ __align__(16) uint32_t s_v[PAIRS ? 512 : 1];
   __shared__ U s_red[2][8];
   __shared__ uint32_t s_redv[2][8];
+  constexpr int kBlockList = 64;
+  __shared__ unsigned int s_blk[kBlockList];   // segments this block's warps leave to it
+  __shared__ int s_nblk;
 
   const int pp = level_parity(P, P.p);
   const unsigned int count = min(P.ctrl->lists[pp].todo, P.l.cap_large);
@@ -321,16 +324,26 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
   };
 
   // Samples of up to 256 keys: one warp per segment sorts them in registers (8 per
-  // lane, a bitonic network without block barriers) and reads off the median.
+  // lane, a bitonic network without block barriers) and reads off the median.  The
+  // other segments a warp meets go on the block's list for the block phase below.
+  // Block b's warps take the entries b, b + gridDim, b + 2 gridDim, ..., so the
+  // segments left to the blocks spread over all of them.
+  if (threadIdx.x == 0) s_nblk = 0;
+  __syncthreads();
+  const unsigned int nw = blockDim.x >> 5;
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned int nw = blockDim.x >> 5;
-    for (unsigned int i = blockIdx.x * nw + warp; i < count; i += gridDim.x * nw) {
+    for (unsigned int i = blockIdx.x + warp * gridDim.x; i < count; i += gridDim.x * nw) {
       const unsigned int s = P.l.todo[pp][i];
       const Seg sg = segs[s];
-      if (sg.depth >= P.depth_limit) continue;
       const int64_t k = sample_size(sg.len);
-      if (k > 256) continue;
+      if (sg.depth >= P.depth_limit || k > 256) {
+        if (lane == 0) {
+          const int j = atomicAdd(&s_nblk, 1);
+          if (j < kBlockList) s_blk[j] = s;
+        }
+        continue;
+      }
       const U* keys = (const U*)P.b.key[sg.parity];
       const uint32_t* vals = P.b.val[sg.parity];
       U x[8];
@@ -364,9 +377,22 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
     }
   }
 
-  // Larger samples and the depth-limit fallback: one block per segment.
-  for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
-    const unsigned int s = P.l.todo[pp][i];
+  // Larger samples and the depth-limit fallback: the whole block per segment, for the
+  // segments its warps listed, or, when the list overflowed, for every such segment
+  // among the entries its warps visited (the same set, read again).
+  __syncthreads();
+  const int nblk = s_nblk;
+  const bool listed = nblk <= kBlockList;
+  const unsigned int rounds = listed ? (unsigned int)nblk : (count + gridDim.x - 1) / gridDim.x;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    unsigned int s;
+    if (listed) {
+      s = s_blk[r];
+    } else {
+      const unsigned int i = blockIdx.x + r * gridDim.x;
+      if (i >= count) continue;
+      s = P.l.todo[pp][i];
+    }
     const Seg sg = segs[s];
     if (sg.depth < P.depth_limit && sample_size(sg.len) <= 256) continue;   // done above
     const U* keys = (const U*)P.b.key[sg.parity];

@@ -150,8 +150,8 @@ def test_local_partition_depth_fallback_and_pairs(bqs, dtype):
 
 def test_pivot_kernel_with_many_block_pivots(bqs):
     # Depth limit 0 sends every large segment to the pivot kernel's block phase; with
-    # cutoff 2 a level holds far more of them than the kernel has blocks, so every
-    # block takes many in turn.
+    # cutoff 2 a level holds far more of them than a block's list takes (64 per block),
+    # so the blocks fall back to reading their entries again.
     bqs.set_option("depth_limit", 0)
     bqs.set_option("small_cutoff", 2)
     for dtype in DTYPES:
