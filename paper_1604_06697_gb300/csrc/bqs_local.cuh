@@ -71,7 +71,8 @@ __device__ __forceinline__ void local_sort_leaves(const SubSeg* leaves, int nlea
       const SubSeg a = leaves[f];
       if (a.len <= kMaxSmall) continue;
       if (k++ % NG != g) continue;
-      group_sort_keys<KT, G::RMAX, G::TBIG, true>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
+      // (a group that is the whole block, 64-bit keys, takes the block barrier)
+      group_sort_keys<KT, G::RMAX, G::TBIG, (G::TBIG < T)>(kb0 + a.begin, fk + a.begin, a.len, gt, sw);
     }
   }
   __syncthreads();   // the staging rows change owners

@@ -108,7 +108,7 @@ def test_local_partition_cutoffs(bqs, cutoff, local, pivot):
 
 
 @pytest.mark.parametrize("local_sort", [0, 1, 128])
-@pytest.mark.parametrize("cutoff", [256, 2048, 4096])
+@pytest.mark.parametrize("cutoff", [256, 2048, 3000, 4096])
 def test_local_sort_of_the_leaves(bqs, cutoff, local_sort):
     # The single-block local partitioning sorts up to `local_sort` finished
     # sub-segments of its segment in shared memory; the others (all with 0) go back to
