@@ -85,19 +85,23 @@ def candidate_configs(kind: str = "sort") -> list:
             if s <= 2048 or (kind != "pairs" and w == 0)]
 
 
-def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int = 2,
+def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int | None = None,
          cache_path: str | None = None, force: bool = False, candidates=None) -> dict:
     """Returns (and caches) the fastest configuration for this workload class.
 
     kind: "sort" (one array of n keys, uniform values), "pairs" (n key-value pairs:
     keys uniform in [0, 2^20), payload = index, sorted by bqs_sort_pairs) or
     "batched" (nseg arrays with log-uniform lengths in [16, 65536] totalling about n
-    keys, sorted by bqs_sort_batched).
+    keys, sorted by bqs_sort_batched).  reps: timed sorts per candidate, the best one
+    kept (default 5 up to 2^22 keys, where one sort takes well under a millisecond
+    and launch jitter decides between close candidates; 2 above).
     """
     import torch
 
     import paper_1604_06697_gb300 as bqs
 
+    if reps is None:
+        reps = 5 if n <= (1 << 22) else 2
     path = cache_path or default_cache_path()
     table = _load(path)
     key = cache_key(dtype, n, kind)
