@@ -7,6 +7,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -107,7 +108,23 @@ struct Variant {
   const void* fn;
   size_t smem;        // dynamic shared memory per block
   void (*launch)(const Params&, int grid, cudaStream_t);
+  void (*prepare)();  // allows its shared memory on the current device (before any use)
 };
+
+// A kernel that takes more than 48 KB of dynamic shared memory has to say so on every
+// device it runs on: the attribute belongs to that device's context.  `devs` (one per
+// kernel) remembers the devices already done; setting it twice is harmless.
+inline void allow_smem_on_device(const void* fn, size_t smem, std::atomic<unsigned long long>& devs) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (devs.load(std::memory_order_acquire) & bit) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  devs.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
 void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
@@ -115,12 +132,19 @@ void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
       <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, st>>>(P);
 }
 
+template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
+void prepare_partition_tma() {
+  static std::atomic<unsigned long long> devs{0};
+  allow_smem_on_device((const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
+                       TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, devs);
+}
+
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK = 256, int MINB = 1>
 Variant make_tma_variant() {
   const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>;
   const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>};
+  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
+                 &prepare_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>};
 }
 
 // Tile shapes offered to the autotuner (BQS_OPT_TILE 0..4), all TMA-fed persistent
@@ -145,6 +169,7 @@ const std::vector<Variant>& variants() {
       r.push_back(make_tma_variant<KT, PAIRS, 256, 4, 4, 128>());
       r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 2, 64, 4>());
     }
+    for (const Variant& x : r) x.prepare();   // every variant on the first device at once
     return r;
   }();
   return v;
@@ -158,13 +183,11 @@ struct LocalCap {
   static constexpr int L = PAIRS ? 4096 : (int)(32768 / sizeof(typename KT::U));
   static constexpr int T = 256;
   static constexpr size_t smem = LocalShape<KT, PAIRS, L, T, SORT>::smem;
-  static const void* fn() {
-    static const void* f = [] {
-      const void* k = (const void*)k_local_partition<KT, PAIRS, L, T, SORT>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      return k;
-    }();
-    return f;
+  static const void* fn() {   // the kernel, its shared memory allowed on the current device
+    static std::atomic<unsigned long long> devs{0};
+    const void* k = (const void*)k_local_partition<KT, PAIRS, L, T, SORT>;
+    allow_smem_on_device(k, smem, devs);
+    return k;
   }
   static int grid();
   static void launch(const Params& P, int p, int grid, cudaStream_t st) {
@@ -471,6 +494,7 @@ int run_call(const Call& c, Stats& st) {
   const cudaStream_t s = (cudaStream_t)c.stream;
   const auto& vars = variants<KT, PAIRS>();
   const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
+  var.prepare();   // before its occupancy query and every launch path below
   const int tile = var.threads * var.kpt;
   // Cutoffs above kMaxSmall apply to key-only sorts with the warp-group networks.
   const int small_cutoff = c.partition_only ? 1
