@@ -58,6 +58,8 @@ def _load():
         lib.oracle_select.restype = ctypes.c_int
         lib.oracle_record_keys.argtypes = [vp, i64, i32, i32, i32, i32, vp]
         lib.oracle_record_keys.restype = ctypes.c_int
+        lib.oracle_pivot_value.argtypes = [vp, i64, i32, i32, i64, i64, vp]
+        lib.oracle_pivot_value.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -71,7 +73,7 @@ def use_library(path: str) -> None:
     lib = ctypes.CDLL(path)
     for name in ("oracle_sort", "oracle_sort_pairs", "oracle_sort_segmented",
                  "oracle_block_partition", "oracle_partition_by_value", "oracle_select",
-                 "oracle_record_keys"):
+                 "oracle_record_keys", "oracle_pivot_value"):
         f, g = getattr(lib, name), getattr(_lib, name)
         f.argtypes, f.restype = g.argtypes, g.restype
     _lib = lib
@@ -173,6 +175,16 @@ def select(keys: np.ndarray, k: int):
     out = np.zeros(1, dtype=a.dtype)
     if _load().oracle_select(_ptr(a), a.size, _dtype_code(a), int(k), _ptr(out)):
         raise ValueError("oracle_select: invalid arguments")
+    return out[0]
+
+
+def pivot_value(keys: np.ndarray, b: int, e: int, pivot: str = "sqrt"):
+    """The pivot the sort chooses for keys[b:e] under a pivot rule (keys unchanged)."""
+    a = np.ascontiguousarray(keys)
+    out = np.zeros(1, dtype=a.dtype)
+    if _load().oracle_pivot_value(_ptr(a), a.size, _dtype_code(a), PIVOT_RULES[pivot], int(b),
+                                  int(e), _ptr(out)):
+        raise ValueError("oracle_pivot_value: invalid arguments")
     return out[0]
 
 

@@ -188,111 +188,135 @@ struct Sorter {
     return median_position(A, medians);
   }
 
-  // ---- block partitioning (Algorithm 3) -------------------------------------------
+  // ---- block partitioning (Sec. 3, Algorithm 3) ---------------------------------------
+
+  // What one side of the partition carries from one round to the next: the positions,
+  // in the order its last scan met them, of the elements of its last block that belong
+  // to the other side and have not been exchanged yet (Sec. 3's offset buffer).
+  struct Side {
+    int64_t misplaced[kB];
+    int64_t head = 0;      // first entry not exchanged yet
+    int64_t pending = 0;   // entries not exchanged yet
+  };
+
+  // Scan phase (Sec. 3): compares `count` elements with the pivot, walking from `from`
+  // upwards (step +1, the left side) or downwards (step -1, the right side), and keeps
+  // the positions of the elements that belong to the other side: >= pivot met on the
+  // left, <= pivot met on the right.  The position is written every time; only the
+  // comparison's outcome decides whether the entry is kept, so the loop body has no
+  // branch on the data.
+  void scan(const T* A, const T& pivot, int64_t from, int64_t count, int step, Side& s) {
+    s.head = 0;
+    s.pending = 0;
+    for (int64_t i = 0; i < count; ++i) {
+      const int64_t at = from + step * i;
+      s.misplaced[s.pending] = at;
+      s.pending += step > 0 ? !lt(A[at], pivot) : !lt(pivot, A[at]);
+    }
+  }
+
+  // Rearrangement phase (Sec. 3): exchanges misplaced elements of the two sides in
+  // pairs, as many pairs as both sides hold.
+  static void exchange(T* A, Side& a, Side& b) {
+    const int64_t pairs = std::min(a.pending, b.pending);
+    for (int64_t j = 0; j < pairs; ++j) std::swap(A[a.misplaced[a.head + j]], A[b.misplaced[b.head + j]]);
+    a.head += pairs;
+    a.pending -= pairs;
+    b.head += pairs;
+    b.pending -= pairs;
+  }
 
   // Partitions A[lo, hi) around the element at position piv.  Returns the pivot's
   // final position p: A[lo, p) <= A[p] <= A(p, hi).
   int64_t block_partition(T* A, int64_t lo, int64_t hi, int64_t piv) {
-    // The pivot is parked at the last position and left out of the scans.
-    std::swap(A[piv], A[hi - 1]);
-    piv = hi - 1;
-    const T pivot = A[piv];
+    // The pivot waits at the last position, outside every scan, until the very end.
+    const int64_t home = hi - 1;
+    std::swap(A[piv], A[home]);
+    const T pivot = A[home];
 
-    int64_t l = lo;       // first element of the not yet partitioned window
-    int64_t r = hi - 2;   // last element of that window (inclusive)
-    int64_t offL[kB], offR[kB];  // offsets of misplaced elements in the current blocks
-    int64_t numL = 0, numR = 0, startL = 0, startR = 0;
-
-    // Main loop: while more than two blocks remain, refill whichever buffer is empty by
-    // scanning a whole block, then swap as many misplaced pairs as both buffers allow.
-    while (r - l + 1 > 2 * kB) {
-      if (numL == 0) {
-        startL = 0;
-        for (int64_t i = 0; i < kB; ++i) {   // left block: collect elements >= pivot
-          offL[numL] = i;
-          numL += !lt(A[l + i], pivot);
-        }
-      }
-      if (numR == 0) {
-        startR = 0;
-        for (int64_t i = 0; i < kB; ++i) {   // right block: collect elements <= pivot
-          offR[numR] = i;
-          numR += !lt(pivot, A[r - i]);
-        }
-      }
-      int64_t m = std::min(numL, numR);
-      for (int64_t j = 0; j < m; ++j) std::swap(A[l + offL[startL + j]], A[r - offR[startR + j]]);
-      numL -= m; numR -= m;
-      startL += m; startR += m;
-      if (numL == 0) l += kB;   // left block done
-      if (numR == 0) r -= kB;   // right block done
+    // [begin, end) is the part of the array whose elements are not yet known to be on
+    // their side.  A side whose last block still holds misplaced elements keeps that
+    // block inside the range, at its own edge.
+    int64_t begin = lo, end = home;
+    Side left, right;
+    while (end - begin > 2 * kB) {
+      // A side that has nothing left to exchange scans its next block ...
+      if (left.pending == 0) scan(A, pivot, begin, kB, +1, left);
+      if (right.pending == 0) scan(A, pivot, end - 1, kB, -1, right);
+      // ... then misplaced pairs are exchanged, and a block with nothing misplaced
+      // left leaves the range.
+      exchange(A, left, right);
+      if (left.pending == 0) begin += kB;
+      if (right.pending == 0) end -= kB;
     }
 
-    // Final scan: the window holds at most 2B elements.  An empty buffer's side is
-    // scanned as a (shorter) block that together with a pending block covers the window.
-    int64_t rest = r - l + 1, shiftL, shiftR;
-    if (numL == 0 && numR == 0) {
-      shiftL = rest / 2;
-      shiftR = rest - shiftL;
-      startL = startR = 0;
-      for (int64_t i = 0; i < shiftL; ++i) { offL[numL] = i; numL += !lt(A[l + i], pivot); }
-      for (int64_t i = 0; i < shiftR; ++i) { offR[numR] = i; numR += !lt(pivot, A[r - i]); }
-    } else if (numR != 0) {      // right block pending: scan the rest on the left
-      shiftL = rest - kB;
-      shiftR = kB;
-      startL = 0;
-      for (int64_t i = 0; i < shiftL; ++i) { offL[numL] = i; numL += !lt(A[l + i], pivot); }
-    } else {                     // left block pending: scan the rest on the right
-      shiftL = kB;
-      shiftR = rest - kB;
-      startR = 0;
-      for (int64_t i = 0; i < shiftR; ++i) { offR[numR] = i; numR += !lt(pivot, A[r - i]); }
+    // At most 2B elements are left.  A side that still has misplaced elements keeps
+    // its block; the other side scans everything else as one shorter block.  When
+    // neither has any, the rest is split into two halves, one per side.
+    const int64_t rest = end - begin;
+    int64_t left_len, right_len;
+    if (left.pending) {
+      left_len = kB;
+      right_len = rest - kB;
+      scan(A, pivot, end - 1, right_len, -1, right);
+    } else if (right.pending) {
+      right_len = kB;
+      left_len = rest - kB;
+      scan(A, pivot, begin, left_len, +1, left);
+    } else {
+      left_len = rest / 2;
+      right_len = rest - left_len;
+      scan(A, pivot, begin, left_len, +1, left);
+      scan(A, pivot, end - 1, right_len, -1, right);
     }
-    int64_t m = std::min(numL, numR);
-    for (int64_t j = 0; j < m; ++j) std::swap(A[l + offL[startL + j]], A[r - offR[startR + j]]);
-    numL -= m; numR -= m;
-    startL += m; startR += m;
-    if (numL == 0) l += shiftL;
-    if (numR == 0) r -= shiftR;
+    exchange(A, left, right);
+    if (left.pending == 0) begin += left_len;
+    if (right.pending == 0) end -= right_len;
 
-    // At most one buffer still holds misplaced elements; the window [l, r] is then
-    // exactly that buffer's block.  Move them to the far end of the block (no more
-    // comparisons), then swap the pivot into the gap.
-    if (numL != 0) {
-      // Elements >= pivot at l + offL[...] go to the right end of [l, r].
-      int64_t upper = r;
-      int64_t k = startL + numL - 1;
-      while (k >= startL && l + offL[k] == upper) { --upper; --k; }   // already in place
-      for (; k >= startL; --k, --upper) std::swap(A[upper], A[l + offL[k]]);
-      std::swap(A[piv], A[upper + 1]);
-      return upper + 1;
+    // Now at most one side still has misplaced elements, and [begin, end) is exactly
+    // the block they are in.  They move to the end of that block that faces the other
+    // side, without further comparisons, and the pivot takes the slot between the two
+    // sides.  Positions are taken nearest-to-that-end first, so every swap moves a
+    // misplaced element past elements that are already on their side.
+    if (left.pending) {   // >= pivot, kept in ascending positions: fill from the top
+      int64_t slot = end;
+      for (int64_t j = left.head + left.pending - 1; j >= left.head; --j)
+        std::swap(A[--slot], A[left.misplaced[j]]);
+      std::swap(A[home], A[slot]);
+      return slot;
     }
-    if (numR != 0) {
-      // Elements <= pivot at r - offR[...] go to the left end of [l, r].
-      int64_t lower = l;
-      int64_t k = startR + numR - 1;
-      while (k >= startR && r - offR[k] == lower) { ++lower; --k; }   // already in place
-      for (; k >= startR; --k, ++lower) std::swap(A[lower], A[r - offR[k]]);
-      std::swap(A[piv], A[lower]);
-      return lower;
+    if (right.pending) {  // <= pivot, kept in descending positions: fill from the bottom
+      int64_t slot = begin;
+      for (int64_t j = right.head + right.pending - 1; j >= right.head; --j)
+        std::swap(A[slot++], A[right.misplaced[j]]);
+      std::swap(A[home], A[slot]);
+      return slot;
     }
-    std::swap(A[piv], A[l]);
-    return l;
+    std::swap(A[home], A[begin]);
+    return begin;
+  }
+
+  // Chooses the pivot of A[b, e) (Sec. 2; Sec. 4 "Different Pivot Selection Methods")
+  // and returns its position.  Median-of-three also puts its three sample elements in
+  // order, which leaves A[b] <= pivot <= A[e-1]; *ends_done then tells the caller that
+  // those two are already on their sides.
+  int64_t choose_pivot(T* A, int64_t b, int64_t e, bool* ends_done) {
+    const int64_t len = e - b;
+    if (pivot_rule == kMedianOf3 || len < 64) {
+      *ends_done = true;
+      return median_of_3(A, b, b + len / 2, e - 1);
+    }
+    *ends_done = false;
+    if (len < 20000) return median_of_5_medians_of_5(A, b, len);
+    return median_position(A, spaced(b, len, isqrt(len) | 1));
   }
 
   // Chooses a pivot for A[b, e) and partitions; returns the pivot's final position.
   int64_t partition(T* A, int64_t b, int64_t e) {
     ++cnt.partitions;
-    int64_t len = e - b;
-    if (pivot_rule == kMedianOf3 || len < 64) {
-      // The sample's minimum and maximum end up at b and e-1, on their correct sides,
-      // so only A[b+1, e-1) is partitioned.
-      int64_t mid = median_of_3(A, b, b + len / 2, e - 1);
-      return block_partition(A, b + 1, e - 1, mid);
-    }
-    int64_t piv = (len < 20000) ? median_of_5_medians_of_5(A, b, len)
-                                : median_position(A, spaced(b, len, isqrt(len) | 1));
-    return block_partition(A, b, e, piv);
+    bool ends_done = false;
+    const int64_t piv = choose_pivot(A, b, e, &ends_done);
+    return ends_done ? block_partition(A, b + 1, e - 1, piv) : block_partition(A, b, e, piv);
   }
 
   // ---- Quicksort main loop --------------------------------------------------------
@@ -334,6 +358,16 @@ template <class T, class Less>
 void run_sort(T* A, int64_t n, int rule, int64_t is_thresh, int64_t depth_limit, Counters& c) {
   Sorter<T, Less> s{c, rule, std::max<int64_t>(is_thresh, 2), depth_limit};
   s.sort(A, n);
+}
+
+// The pivot value the sort would choose for A[b, e) of a copy of keys[0, n).
+template <class T, class Less>
+void run_pivot_value(const T* keys, int64_t n, int rule, int64_t b, int64_t e, T* out) {
+  Counters c;
+  Sorter<T, Less> s{c, rule, 16, -1};
+  std::vector<T> a(keys, keys + n);
+  bool ends_done = false;
+  *out = a[s.choose_pivot(a.data(), b, e, &ends_done)];
 }
 
 template <class T, class Less>
@@ -441,6 +475,20 @@ int64_t oracle_block_partition(void* keys, int64_t n, int32_t dtype, int64_t piv
   }
   export_counters(c, counters);
   return p;
+}
+
+// The pivot the sort chooses for the sub-array keys[b, e) (e - b >= 3) under a pivot
+// rule (0 = median-of-3, 1 = sqrt(n)), written to *out; keys are not changed.  A test
+// entry: it exposes the pivot rules of Sec. 2 and Sec. 4 to their pins.
+int oracle_pivot_value(const void* keys, int64_t n, int32_t dtype, int32_t pivot_rule, int64_t b,
+                       int64_t e, void* out) {
+  if (!keys || !out || b < 0 || e > n || e - b < 3 || pivot_rule < 0 || pivot_rule > 1) return -1;
+  switch (dtype) {
+    case 0: run_pivot_value<int32_t, LessI32>((const int32_t*)keys, n, pivot_rule, b, e, (int32_t*)out); return 0;
+    case 1: run_pivot_value<int64_t, LessI64>((const int64_t*)keys, n, pivot_rule, b, e, (int64_t*)out); return 0;
+    case 2: run_pivot_value<double, LessF64>((const double*)keys, n, pivot_rule, b, e, (double*)out); return 0;
+    default: return -1;
+  }
 }
 
 // The key that a sorted copy of keys[0, n) holds at position k (the k-th order statistic,

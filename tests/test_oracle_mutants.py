@@ -17,20 +17,20 @@ SRC = os.path.join(ROOT, "oracle", "bqs_oracle.cpp")
 
 # (name, original text, planted mistake)
 MUTANTS = [
-    ("left scan direction", "numL += !lt(A[l + i], pivot);\n        }",
-     "numL += lt(A[l + i], pivot);\n        }"),
-    ("right scan direction", "numR += !lt(pivot, A[r - i]);\n        }",
-     "numR += lt(pivot, A[r - i]);\n        }"),
-    ("left block advance", "if (numL == 0) l += kB;", "if (numL == 0) l += kB - 1;"),
-    ("final split of the rest", "shiftL = rest / 2;", "shiftL = rest / 2 + (rest > 3);"),
-    ("compaction pivot slot", "std::swap(A[piv], A[upper + 1]);\n      return upper + 1;",
-     "std::swap(A[piv], A[upper]);\n      return upper;"),
-    ("right compaction skip", "while (k >= startR && r - offR[k] == lower) { ++lower; --k; }",
-     "while (k >= startR && r - offR[k] == lower) { lower += 2; --k; }"),
-    ("median-of-3 sample", "int64_t mid = median_of_3(A, b, b + len / 2, e - 1);",
-     "int64_t mid = median_of_3(A, b, b + len / 2, e - 2);"),
-    ("pivot = first element", "int64_t mid = median_of_3(A, b, b + len / 2, e - 1);",
-     "int64_t mid = b;"),
+    ("left scan direction", "s.pending += step > 0 ? !lt(A[at], pivot) : !lt(pivot, A[at]);",
+     "s.pending += step > 0 ? lt(A[at], pivot) : !lt(pivot, A[at]);"),
+    ("right scan direction", "s.pending += step > 0 ? !lt(A[at], pivot) : !lt(pivot, A[at]);",
+     "s.pending += step > 0 ? !lt(A[at], pivot) : lt(pivot, A[at]);"),
+    ("left block advance", "if (left.pending == 0) begin += kB;", "if (left.pending == 0) begin += kB - 1;"),
+    ("final split of the rest", "right_len = rest - left_len;\n      scan(A, pivot, begin, left_len",
+     "right_len = rest - left_len - (rest > 3);\n      scan(A, pivot, begin, left_len"),
+    ("compaction pivot slot", "std::swap(A[--slot], A[left.misplaced[j]]);\n      std::swap(A[home], A[slot]);",
+     "std::swap(A[--slot], A[left.misplaced[j]]);\n      std::swap(A[home], A[slot - 1]);"),
+    ("right compaction start", "int64_t slot = begin;", "int64_t slot = begin + 1;"),
+    ("median-of-3 sample", "return median_of_3(A, b, b + len / 2, e - 1);",
+     "return median_of_3(A, b, b + len / 2, e - 2);"),
+    ("pivot = first element", "return median_of_3(A, b, b + len / 2, e - 1);",
+     "return b;"),
     ("pivot not excluded", "stack.push_back({b, p, depth});\n          b = p + 1;",
      "stack.push_back({b, p, depth});\n          b = p;"),
     ("heap child choice", "if (child + 1 < n && lt(H[child], H[child + 1])) ++child;",
@@ -48,6 +48,20 @@ MUTANTS = [
     ("record norm components", "for (int32_t c = 0; c < count; ++c) {\n        double x;",
      "for (int32_t c = 1; c < count; ++c) {\n        double x;"),
     ("record key field", "std::memcpy(&v, r, 4);", "std::memcpy(&v, r + 4, 4);"),
+    # the pivot rules of Sec. 4: group size, sample positions, the 20000 switch, sample size
+    ("mo5-of-mo5 groups of three", "p.begin() + 5 * g, p.begin() + 5 * g + 5)",
+     "p.begin() + 5 * g, p.begin() + 5 * g + 3)"),
+    ("sample positions i*len/k", "p[i] = b + ((2 * i + 1) * len) / (2 * k);",
+     "p[i] = b + (i * len) / k;"),
+    ("sqrt switch at 2000", "if (len < 20000) return median_of_5_medians_of_5(A, b, len);",
+     "if (len < 2000) return median_of_5_medians_of_5(A, b, len);"),
+    ("sqrt switch at or above 20000", "if (len < 20000) return median_of_5_medians_of_5(A, b, len);",
+     "if (len <= 20000) return median_of_5_medians_of_5(A, b, len);"),
+    ("half-size sqrt sample", "spaced(b, len, isqrt(len) | 1)", "spaced(b, len, (isqrt(len) / 2) | 1)"),
+    ("sample offset dropped", "p[i] = b + ((2 * i + 1) * len) / (2 * k);",
+     "p[i] = ((2 * i + 1) * len) / (2 * k);"),
+    ("mo3 switch below 64", "if (pivot_rule == kMedianOf3 || len < 64) {",
+     "if (pivot_rule == kMedianOf3 || len < 32) {"),
 ]
 
 _RUNNER = r"""
@@ -75,6 +89,13 @@ pins = [
     lambda: P.test_default_depth_limit_is_the_papers(1 << 10),
     lambda: P.test_select_is_the_order_statistic("int32"),
     lambda: P.test_record_keys_follow_their_definition(),
+    lambda: P.test_sqrt_sample_size_and_positions(0, 1000),
+    lambda: P.test_sqrt_sample_size_and_positions(1, 0),
+    lambda: P.test_median_of_5_medians_of_5_below_20000(0, 333),
+    lambda: P.test_median_of_5_medians_of_5_below_20000(1, 0),
+    lambda: P.test_median_of_5_medians_of_5_below_20000(3, 0),
+    lambda: P.test_sqrt_rule_takes_over_at_20000(),
+    lambda: P.test_median_of_3_sample(0),
 ]
 for i, pin in enumerate(pins):
     try:

@@ -358,3 +358,74 @@ def test_sorted_records_are_ordered_by_key_then_position(kind, rb, count):
     keys = oracle.record_keys(rec, rb, kind, 0, count)
     order = sorted(range(n), key=lambda i: (keys[i], i))
     assert np.array_equal(got, rec.reshape(n, rb)[order])
+
+
+# ---- pivot rules on hand-worked samples (Sec. 2; Sec. 4 "Different Pivot Selection Methods") ----
+#
+# tests/golden/pivot_samples.json lists, for a few lengths, the positions the rules
+# sample (derived by hand there) and values to plant at them in an otherwise all-zero
+# array.  A rule that samples other positions, groups them otherwise, sizes its sample
+# otherwise or switches at another length sees mostly zeros or other groups, and
+# returns another pivot.
+
+def _pivot_golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pivot_samples.json")) as f:
+        return json.load(f)
+
+
+def _planted(length, b, positions, values, dtype="int32", total_pad=37):
+    a = np.zeros(b + length + total_pad, dtype=dtype)
+    for p, v in zip(positions, values):
+        assert 0 <= p < length
+        a[b + p] = v
+    return a
+
+
+@pytest.mark.parametrize("b", [0, 1000])
+@pytest.mark.parametrize("case", [0, 1])
+def test_sqrt_sample_size_and_positions(case, b):
+    g = _pivot_golden()["sqrt_sample"][case]
+    k, stride = g["k"], g["stride"]
+    positions = [stride * (2 * i + 1) for i in range(k)]
+    values = [1 + (37 * i) % k for i in range(k)]
+    for dtype in DTYPES:
+        a = _planted(g["len"], b, positions, values, dtype)
+        got = oracle.pivot_value(a, b, b + g["len"], "sqrt")
+        assert got == g["pivot"], (g["len"], b, dtype, got)
+
+
+@pytest.mark.parametrize("b", [0, 333])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_median_of_5_medians_of_5_below_20000(case, b):
+    g = _pivot_golden()["mo5_of_mo5"]
+    c = g["cases"][case]
+    if "stride" in c:
+        positions = [c["stride"] * (2 * i + 1) + c["shift"] for i in range(25)]
+    else:
+        positions = c["positions"]
+    a = _planted(c["len"], b, positions, g["values"])
+    got = oracle.pivot_value(a, b, b + c["len"], c["rule"])
+    assert got == g["pivot"], (c["len"], b, got)
+
+
+def test_sqrt_rule_takes_over_at_20000():
+    g, s = _pivot_golden()["mo5_of_mo5"], _pivot_golden()["switch_at_20000"]
+    positions = [s["stride"] * (2 * i + 1) + s["shift"] for i in range(25)]
+    a = _planted(s["len"], 0, positions, g["values"])
+    assert oracle.pivot_value(a, 0, s["len"], "sqrt") == s["pivot"]
+    # the same planted values one element shorter are read as median-of-5-medians-of-5
+    # (19999: positions 400 (2i+1) - 1)
+    c = g["cases"][2]
+    positions = [c["stride"] * (2 * i + 1) + c["shift"] for i in range(25)]
+    a = _planted(c["len"], 0, positions, g["values"])
+    assert oracle.pivot_value(a, 0, c["len"], "sqrt") == g["pivot"]
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_median_of_3_sample(case):
+    c = _pivot_golden()["mo3"][case]
+    for b in (0, 70):
+        a = _planted(c["len"], b, c["positions"], c["values"])
+        assert oracle.pivot_value(a, b, b + c["len"], c["rule"]) == c["pivot"]
