@@ -147,7 +147,9 @@ int bqs_sort_pairs(void* keys, uint32_t* vals, int64_t n, int32_t dtype, bqs_str
  * cudaMallocHost or cudaFree call.  The first call on a device looks up that array's
  * device address for
  * the device (cudaGetSymbolAddress) and sets up the kernels; make that first call
- * before any stream capture.  All calls share the one array and every call starts
+ * before any stream capture.  A call on a stream that is being captured into a CUDA
+ * graph returns BQS_ERR_UNSUPPORTED and enqueues nothing (the caller's capture stays
+ * valid).  All calls share the one array and every call starts
  * by clearing the parts it relies on, so earlier contents do not matter, but calls
  * whose work overlaps on the GPU (different streams or threads at the same time)
  * race on it: serialise them.  Synchronous with respect to `stream` between

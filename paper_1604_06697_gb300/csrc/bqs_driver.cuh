@@ -108,22 +108,26 @@ struct Variant {
   const void* fn;
   size_t smem;        // dynamic shared memory per block
   void (*launch)(const Params&, int grid, cudaStream_t);
-  void (*prepare)();  // allows its shared memory on the current device (before any use)
+  cudaError_t (*prepare)();  // allows its shared memory on the current device (before any use)
 };
 
 // A kernel that takes more than 48 KB of dynamic shared memory has to say so on every
 // device it runs on: the attribute belongs to that device's context.  `devs` (one per
-// kernel) remembers the devices already done; setting it twice is harmless.
-inline void allow_smem_on_device(const void* fn, size_t smem, std::atomic<unsigned long long>& devs) {
+// kernel) remembers the devices on which it was set; a failed attribute call is
+// returned (and tried again by the next call), and a device index outside 0..63 is
+// refused rather than mistaken for another device.
+inline cudaError_t allow_smem_on_device(const void* fn, size_t smem,
+                                        std::atomic<unsigned long long>& devs) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    dev = 0;
-  }
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const unsigned long long bit = 1ull << dev;
-  if (devs.load(std::memory_order_acquire) & bit) return;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (devs.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   devs.fetch_or(bit, std::memory_order_acq_rel);
+  return cudaSuccess;
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
@@ -133,10 +137,10 @@ void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
-void prepare_partition_tma() {
+cudaError_t prepare_partition_tma() {
   static std::atomic<unsigned long long> devs{0};
-  allow_smem_on_device((const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
-                       TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, devs);
+  return allow_smem_on_device((const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
+                              TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, devs);
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK = 256, int MINB = 1>
@@ -169,7 +173,10 @@ const std::vector<Variant>& variants() {
       r.push_back(make_tma_variant<KT, PAIRS, 256, 4, 4, 128>());
       r.push_back(make_tma_variant<KT, PAIRS, 256, 8, 2, 64, 4>());
     }
-    for (const Variant& x : r) x.prepare();   // every variant on the first device at once
+    // Every variant on the first device at once; a failure here is returned by the
+    // prepare() call that each sort makes for its own variant.
+    for (const Variant& x : r) (void)x.prepare();
+    cudaGetLastError();
     return r;
   }();
   return v;
@@ -183,15 +190,15 @@ struct LocalCap {
   static constexpr int L = PAIRS ? 4096 : (int)(32768 / sizeof(typename KT::U));
   static constexpr int T = 256;
   static constexpr size_t smem = LocalShape<KT, PAIRS, L, T, SORT>::smem;
-  static const void* fn() {   // the kernel, its shared memory allowed on the current device
+  static const void* fn() { return (const void*)k_local_partition<KT, PAIRS, L, T, SORT>; }
+  // Allows the kernel's shared memory on the current device; called before its
+  // occupancy is queried or it is launched there.
+  static cudaError_t prepare() {
     static std::atomic<unsigned long long> devs{0};
-    const void* k = (const void*)k_local_partition<KT, PAIRS, L, T, SORT>;
-    allow_smem_on_device(k, smem, devs);
-    return k;
+    return allow_smem_on_device(fn(), smem, devs);
   }
   static int grid();
   static void launch(const Params& P, int p, int grid, cudaStream_t st) {
-    fn();
     k_local_partition<KT, PAIRS, L, T, SORT><<<grid, T, smem, st>>>(P, p);
   }
 };
@@ -226,6 +233,16 @@ inline int sm_count() {
 template <class KT, bool PAIRS, bool SORT>
 int LocalCap<KT, PAIRS, SORT>::grid() {
   return persistent_grid(fn(), T, smem);
+}
+
+// Allows the shared memory of the single-block local partitioning kernels that a call
+// with these parameters may launch, on the current device.
+template <class KT, bool PAIRS>
+cudaError_t prepare_local(const Params& P) {
+  if constexpr (!PAIRS) {
+    if (P.local_sort) return LocalCap<KT, false, true>::prepare();
+  }
+  return LocalCap<KT, PAIRS, false>::prepare();
 }
 
 // Launches the single-block local partitioning over the `local` list of parity p:
@@ -494,7 +511,10 @@ int run_call(const Call& c, Stats& st) {
   const cudaStream_t s = (cudaStream_t)c.stream;
   const auto& vars = variants<KT, PAIRS>();
   const Variant& var = vars[(size_t)std::min<int64_t>(std::max<int64_t>(c.opt.tile_variant, 0), (int64_t)vars.size() - 1)];
-  var.prepare();   // before its occupancy query and every launch path below
+  {   // before its occupancy query and every launch path below
+    const cudaError_t e = var.prepare();
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute (partition kernel)");
+  }
   const int tile = var.threads * var.kpt;
   // Cutoffs above kMaxSmall apply to key-only sorts with the warp-group networks.
   const int small_cutoff = c.partition_only ? 1
@@ -563,6 +583,10 @@ int run_call(const Call& c, Stats& st) {
     int lg = 0;
     while (top > 1) { top >>= 1; ++lg; }
     P.depth_limit = c.opt.depth_limit >= 0 ? (int)c.opt.depth_limit : 2 * lg + 3;
+  }
+  if (local_cutoff > small_cutoff) {
+    const cudaError_t e = prepare_local<KT, PAIRS>(P);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute (local partitioning)");
   }
 
   // On a stream that is being captured into a CUDA graph the level loop runs on the

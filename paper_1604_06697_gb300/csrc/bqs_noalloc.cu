@@ -57,6 +57,13 @@ extern "C" int bqs_sort_noalloc(void* keys, int64_t n, int32_t dtype, bqs_stream
   if (dtype < BQS_INT32 || dtype > BQS_FLOAT64 || n < 0) return BQS_ERR_INVALID;
   if (n > kNoAllocMaxKeys) return BQS_ERR_TOO_LARGE;
   clear_stats();
+  // The level loop reads counts back from the device between levels, which a stream
+  // that is being captured into a CUDA graph cannot do; such a call is refused before
+  // anything is enqueued, so the caller's capture stays valid.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+  if (ce != cudaSuccess) return fail_cuda(ce, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone) return BQS_ERR_UNSUPPORTED;
   if (n <= 1) return BQS_OK;
   if (!keys || ((uintptr_t)keys & 15u)) return BQS_ERR_INVALID;
   void* ws = nullptr;
