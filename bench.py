@@ -53,7 +53,7 @@ def parse_args(argv=None):
                              "structured", "records"],
                     help="sort (the default headline line), pairs, batched, serving, matrix, "
                          "pivots, structured or records")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and use --tile/--small/--local instead")
     ap.add_argument("--tile", type=int, default=None)
@@ -66,6 +66,18 @@ def parse_args(argv=None):
 
 def workload_name(a) -> str:
     return f"bqs_sort 2^{a.log2n} {a.dtype} {a.dist} seed {a.seed}, {a.pivot} pivot"
+
+
+def workload_config(a) -> dict:
+    """The workload both arms run, identical in both JSON lines."""
+    n = 1 << a.log2n
+    nbytes = n * (4 if a.dtype == "int32" else 8)
+    size = "2^%d-key (%.1f MiB) array" % (a.log2n, nbytes / 2**20)
+    l2 = ("inputs larger than L2: every step sorts its own unsorted copy of the " + size
+          if nbytes > (129 << 20) else
+          "input smaller than L2: every step sorts its own unsorted copy of the " + size)
+    return {"workload": workload_name(a), "n": n, "dtype": a.dtype, "dist": a.dist,
+            "seed": a.seed, "pivot": a.pivot, "l2": l2}
 
 
 def measured_peak_gbs():
@@ -154,33 +166,30 @@ def pinned_near_gpu(dev, make):
             os.sched_setaffinity(0, saved)
 
 
-def time_oracle(a, seconds: float):
-    """Sorts 2^24-key samples of the workload with the oracle until `seconds` have passed."""
+def time_oracle(a, host_keys, min_seconds: float = 0.0):
+    """Sorts the whole workload with the oracle, single threaded, on a fresh copy each
+    time, at least once and until min_seconds of sorting have passed."""
     import oracle
-    from paper_1604_06697_gb300 import inputs
 
     oracle.build()
-    m = min(1 << 24, 1 << a.log2n)
-    sample = inputs.make_keys(m, a.dtype, a.dist, a.seed)
-    keys = 0
-    t0 = time.perf_counter()
-    reps = 0
+    work = np.empty_like(host_keys)
+    reps, t_sort = 0, 0.0
     while True:
-        oracle.sort(sample, pivot=a.pivot)
-        keys += m
+        work[:] = host_keys
+        t0 = time.perf_counter()
+        oracle.sort_inplace(work, pivot=a.pivot)
+        t_sort += time.perf_counter() - t0
         reps += 1
-        if time.perf_counter() - t0 >= seconds:
+        if t_sort >= min_seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": keys / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x oracle sort of the first 2^{int(math.log2(m))} keys of the "
-                      f"workload ({a.dtype} {a.dist} seed {a.seed}, {a.pivot} pivot), "
-                      f"single thread, {dt:.1f} s"}
+    return {"value": host_keys.size * reps / t_sort, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x oracle sort of the whole 2^{a.log2n}-key workload ({a.dtype} "
+                      f"{a.dist} seed {a.seed}, {a.pivot} pivot), single thread, {t_sort:.1f} s"}
 
 
 def time_library_sorts(a, host_keys, seconds: float):
-    """std::sort on one host thread and a parallel sort on every host core, each on
-    the full workload (or a 2^24-key prefix if one std::sort would take too long)."""
+    """std::sort on one host thread and a parallel sort on every host core, each on the
+    whole workload (at least once, up to three times while under seconds / 2)."""
     import numpy as np
 
     from oracle import cpu_baselines
@@ -189,7 +198,7 @@ def time_library_sorts(a, host_keys, seconds: float):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     out = []
     for threads in (1, cores):
-        m = host_keys.size if threads > 1 or host_keys.size <= (1 << 26) else 1 << 24
+        m = host_keys.size
         keys, reps, t_sort = 0, 0, 0.0
         work = np.empty(m, host_keys.dtype)
         kind = ""
@@ -203,7 +212,7 @@ def time_library_sorts(a, host_keys, seconds: float):
             if t_sort >= seconds / 2 or reps >= 3:
                 break
         out.append({"value": keys / t_sort, "unit": "keys/s", "cores": threads, "kind": kind,
-                    "sample": f"{reps} x {kind} of the first 2^{int(math.log2(m))} keys of the "
+                    "sample": f"{reps} x {kind} of the whole 2^{int(math.log2(m))}-key "
                               f"workload, {threads} thread(s), {t_sort:.1f} s"})
     return out
 
@@ -288,22 +297,45 @@ class ClockSampler:
 # ---- reference arm -------------------------------------------------------------------------------
 
 def run_reference(a):
+    """The reference arm: the paper's algorithm as the single-threaded CPU oracle, on
+    this host, on the same workload and config as our arm.  Every timed step sorts its
+    own unsorted copy of the whole array; the warm-up steps sort its first 2^20 keys
+    (the oracle has nothing to warm up but its code and the input's pages)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = max(1.0, 20.0 / max(1, a.steps + a.warmup))
-    base = time_oracle(a, per_step * (a.steps + a.warmup))
-    value = base["value"]
+    import oracle
+    from paper_1604_06697_gb300 import inputs
+
+    oracle.build()
     n = 1 << a.log2n
+    host = inputs.make_keys(n, a.dtype, a.dist, a.seed)
+    work = np.empty_like(host)
+    m = min(n, 1 << 20)
+    for _ in range(a.warmup):
+        work[:m] = host[:m]
+        oracle.sort_inplace(work[:m], pivot=a.pivot)
+    step_s = []
+    for _ in range(a.steps):
+        work[:] = host
+        t0 = time.perf_counter()
+        oracle.sort_inplace(work, pivot=a.pivot)
+        step_s.append(time.perf_counter() - t0)
+    ok = bool(np.all(work[1:] >= work[:-1])) if a.dtype != "float64" else True
+    total = sum(step_s)
+    value = n * a.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": 1e3 * n / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
-        "config": {"workload": workload_name(a), "n": n, "dist": a.dist, "seed": a.seed,
-                   "pivot": a.pivot},
-        "cpu_baseline": base,
+        "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{a.steps} timed steps, each one oracle sort of the whole "
+                                   f"2^{a.log2n}-key workload on its own unsorted copy, single "
+                                   f"thread ({a.warmup} warm-up steps on its first 2^20 keys)"},
         "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "step_seconds": [round(x, 3) for x in step_s], "sorted_check": ok,
     }
     print(json.dumps(line), flush=True)
 
@@ -360,6 +392,7 @@ def run_ours(a):
     torch.cuda.synchronize(dev)
     bqs.set_option("timing", 1)
     part_ms, part_bytes, launches, part_launches, levels = 0.0, 0.0, 0, 0, []
+    active_keys = 0
     clk = ClockSampler(dev.index if dev.index is not None else 0)
     barrier()
     torch.cuda.synchronize(dev)
@@ -375,6 +408,7 @@ def run_ours(a):
             part_bytes += s["partition_bytes"]
             launches += s["kernel_launches"]
             part_launches += s["partition_launches"]
+            active_keys += s["active_keys"]
             levels.append(s["levels"])
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -476,7 +510,7 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu = time_oracle(a, a.cpu_seconds)
+        cpu = time_oracle(a, host)
         cpu["library_sorts"] = time_library_sorts(a, host, a.cpu_seconds)
 
     peak, peak_kind = measured_peak_gbs()
@@ -498,16 +532,29 @@ def run_ours(a):
         "achieved_isolated": isolated,
         "frac_isolated": (isolated / peak) if isolated else None,
     }
+    # The whole sort against the same peaks: every partition level reads and writes its
+    # active keys once, and every key is read and written once more by its final pass
+    # (network, single-block partitioning or pivot-class fill): sum over levels of
+    # 2 s n_active + 2 s n, divided by the measured time per sort.
+    s_key = host.itemsize
+    sort_bytes = 2.0 * s_key * (active_keys / max(1, a.steps) + n)
+    sort_gbs = sort_bytes / (ms / a.steps / 1e3) / 1e9
+    roofline["sort"] = {
+        "algorithmic_bytes_per_sort": sort_bytes,
+        "formula": "sum over partition levels of 2*sizeof(key)*active keys + 2*sizeof(key)*n",
+        "achieved": sort_gbs, "unit": "GB/s", "frac": sort_gbs / peak,
+        "peak_source": roofline["peak_source"],
+        "frac_of_8tbs_spec": sort_gbs / 8000.0,
+    }
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": a.dtype, "data": "synthetic",
-            "config": {"workload": workload_name(a), "n": n, "dist": a.dist, "seed": a.seed,
-                       "pivot": a.pivot, "autotuned": tuned,
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (one resident 2^%d-key copy per step)" % a.log2n},
+            "config": workload_config(a),
+            "launch_shape": tuned,
+            "parallelism": "replicas" if world > 1 else "single GPU",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "levels_per_sort": levels[0] if levels else None,
             "clocks": clk.summary(), "sorted_check": ok,
@@ -621,6 +668,16 @@ def run_batched(a):
     ok = all(np.array_equal(out[off[i]:off[i + 1]], np.sort(keys[off[i]:off[i + 1]]))
              for i in range(0, nseg, 997))
 
+    # Second baseline: the same batch in one bqs_sort_segmented call on an ordinary
+    # stream (the host drives the level loop): how much of the gain is the graph.
+    seg_bufs = [src.clone() for _ in range(a.steps)]
+    for _ in range(a.warmup):
+        warm.copy_(src)
+        bqs.sort_segmented(warm, toff)
+    seg_ms = _cuda_ms(lambda: [bqs.sort_segmented(b, toff) for b in seg_bufs])
+    seg_ok = bool(np.array_equal(seg_bufs[0].cpu().numpy(), out))
+    del seg_bufs
+
     # Baseline: one bqs_sort call per array (arrays placed at 16-byte aligned offsets).
     lens = np.diff(off)
     poff = np.zeros(nseg + 1, np.int64)
@@ -642,6 +699,11 @@ def run_batched(a):
                    "total_keys": n, "autotuned": tuned["config"], "pivot": "sqrt"},
         "baseline_one_call_per_array": {"value": n / (base_ms / 1e3), "unit": "keys/s",
                                         "ms": base_ms, "calls": nseg},
+        "baseline_one_segmented_call": {"value": n * a.steps / (seg_ms / 1e3), "unit": "keys/s",
+                                        "ms": seg_ms / a.steps, "same_output": seg_ok,
+                                        "how": "bqs_sort_segmented, not captured: the host "
+                                               "reads each level's counts"},
+        "speedup_vs_one_segmented_call": (seg_ms / a.steps) / (ms / a.steps),
         "speedup_vs_per_array": base_ms / (ms / a.steps), "sorted_check": ok}), flush=True)
 
 
@@ -804,15 +866,19 @@ def run_serving(a):
             offered = sum(r.size for r in reqs) / max(r.arrival for r in reqs)
             rep = serving.ServingLoop(pool, mode=mode, slots=3, hbm_budget=64 << 30,
                                       max_batch_keys=1 << 27).run(reqs)
-            row[mode] = {k: rep[k] for k in ("p50_ms", "p99_ms", "served_keys_per_s",
-                                             "batches", "hbm_peak_bytes")}
+            row[mode] = {k: rep[k] for k in ("p50_ms", "p99_ms", "queue_p50_ms", "queue_p99_ms",
+                                             "served_keys_per_s", "offered_keys_per_s", "slots",
+                                             "batches", "requests", "hbm_peak_bytes")}
             row["offered_keys_per_s"] = offered
         rows.append(row)
     print(json.dumps({
         "workload": "serving", "metric": "p50/p99 latency and served keys/s, batched vs plain",
         "unit": "ms / keys/s", "requests_per_rate": a.serve_requests, "data": "synthetic",
         "config": {"sizes": "floor(2^U(10,26))", "dtypes": "uniform over int32/int64/float64",
-                   "arrivals": "Poisson", "hbm_budget_bytes": 64 << 30, "slots": 3, "seed": 3},
+                   "arrivals": "Poisson", "hbm_budget_bytes": 64 << 30, "slots": 3, "seed": 3,
+                   "admission": "keys copied into HBM on a copy stream; the slot waits on "
+                                "the copy's event on the device",
+                   "plain": "one bqs_sort per request on the same 3 slots"},
         "rates": rows}), flush=True)
 
 

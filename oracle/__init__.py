@@ -116,6 +116,16 @@ def sort(keys: np.ndarray, pivot: str = "mo3", is_thresh: int = 16,
     return a
 
 
+def sort_inplace(keys: np.ndarray, pivot: str = "mo3") -> None:
+    """Sorts a contiguous int32/int64/float64 array in place by BlockQuicksort (the same
+    routine as sort(), without the copy; used to time the oracle)."""
+    if not keys.flags["C_CONTIGUOUS"]:
+        raise ValueError("sort_inplace needs a contiguous array")
+    if _load().oracle_sort(_ptr(keys), keys.size, _dtype_code(keys), PIVOT_RULES[pivot], 16, -1,
+                           None):
+        raise ValueError("oracle_sort: invalid arguments")
+
+
 def sort_pairs(keys: np.ndarray, vals: np.ndarray, pivot: str = "mo3"):
     """Sorts (key, payload) pairs lexicographically; returns (keys, vals) copies."""
     k = np.ascontiguousarray(keys).copy()

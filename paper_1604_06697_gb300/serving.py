@@ -13,12 +13,16 @@ as they become free:
   picked up by the next free slot, so work from different batches overlaps on the
   device.
 * ``mode="plain"``: the baseline -- one ``bqs_sort`` call per request, first come
-  first served, on a single stream.
+  first served, on the same number of slots, so the two modes differ only in batching.
 
-Latency of a request = time its sort finished on the GPU (a CUDA event, placed on
-the host clock through a reference event) minus its arrival time; it includes the
-time spent waiting for admission and for a slot.  Every sort runs in the library's
-kernels; this module only schedules.
+Admission copies a request's keys into HBM on a copy stream of its own and records an
+event; the slot that later sorts the request waits for that event on the device, so
+an arrival never waits behind a running sort.  Latency of a request = time its sort
+finished on the GPU (a CUDA event, placed on the host clock through a reference
+event) minus its arrival time; it includes the time spent waiting for admission and
+for a slot (reported on its own as the queue delay: arrival to the moment a slot
+takes the request).  Every sort runs in the library's kernels; this module only
+schedules.
 """
 from __future__ import annotations
 
@@ -47,6 +51,10 @@ class Request:
     @property
     def latency(self) -> float:
         return self.done - self.arrival
+
+    @property
+    def queue_delay(self) -> float:
+        return self.started - self.arrival
 
 
 ITEM = {"int32": 4, "int64": 8, "float64": 8}
@@ -143,7 +151,7 @@ class ServingLoop:
             raise ValueError("mode must be 'batched' or 'plain'")
         self.pool = pool
         self.mode = mode
-        self.slots = 1 if mode == "plain" else slots
+        self.slots = slots
         self.admission = Admission(hbm_budget)
         self.max_batch_keys = max_batch_keys
         self.keep_results = keep_results
@@ -156,6 +164,7 @@ class ServingLoop:
         reqs = sorted(requests, key=lambda r: r.arrival)
         dev = torch.device("cuda")
         streams = [torch.cuda.Stream(dev) for _ in range(self.slots)]
+        copy_stream = torch.cuda.Stream(dev)     # admission copies only
         waiting = collections.deque()       # admitted, not yet started
         pending = collections.deque(reqs)   # not yet arrived or not yet admitted
         cv = threading.Condition()
@@ -193,6 +202,9 @@ class ServingLoop:
                         batch_id[0] += 1
                     start = now()
                     with torch.cuda.stream(stream):
+                        for r in batch:   # its keys have landed in HBM
+                            stream.wait_event(r._ready)
+                            r._buf.record_stream(stream)
                         if self.mode == "plain":
                             r = batch[0]
                             buf = r._buf
@@ -219,6 +231,7 @@ class ServingLoop:
                             r.batch = bid
                             r.result = v if self.keep_results else None
                             r._buf = None
+                            r._ready = None
                             self.admission.release(request_bytes(r.size, r.dtype))
                             finished.append(r)
                         cv.notify_all()
@@ -244,10 +257,10 @@ class ServingLoop:
                     continue
                 pending.popleft()
                 r.admitted = now()
-                with torch.cuda.stream(streams[0]):
+                with torch.cuda.stream(copy_stream):
                     r._buf = self.pool.keys(r).clone()   # the request's keys, now in HBM
-                torch.cuda.current_stream().wait_stream(streams[0])
-                streams[0].synchronize()
+                    r._ready = torch.cuda.Event()
+                    r._ready.record(copy_stream)
                 with cv:
                     waiting.append(r)
                     cv.notify_all()
@@ -263,13 +276,17 @@ class ServingLoop:
 
     def report(self, finished, wall):
         lat = [r.latency for r in finished]
+        queue = [r.queue_delay for r in finished]
         keys = sum(r.size for r in finished)
         span = max(r.done for r in finished) - min(r.arrival for r in finished) if finished else math.nan
+        arrivals = max(r.arrival for r in finished) - min(r.arrival for r in finished) if finished else math.nan
         batches = len({r.batch for r in finished})
         return {
-            "mode": self.mode, "requests": len(finished), "batches": batches,
+            "mode": self.mode, "slots": self.slots, "requests": len(finished), "batches": batches,
             "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
             "mean_ms": 1e3 * (sum(lat) / len(lat)) if lat else math.nan,
+            "queue_p50_ms": 1e3 * percentile(queue, 50), "queue_p99_ms": 1e3 * percentile(queue, 99),
+            "offered_keys_per_s": keys / arrivals if arrivals and arrivals > 0 else math.nan,
             "served_keys_per_s": keys / span if span and span > 0 else math.nan,
             "keys": keys, "span_s": span, "wall_s": wall,
             "hbm_peak_bytes": self.admission.peak, "hbm_budget_bytes": self.admission.budget,

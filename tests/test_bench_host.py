@@ -38,3 +38,15 @@ def test_autotune_candidates_cover_every_knob_once():
         per_cutoff = len(autotune.TILES) * len(autotune.LOCAL_CUTOFFS) * len(autotune.OVERLAPS)
         assert len(big) == (0 if kind == "pairs" else per_cutoff)
         assert len(cands) - len(big) == per_cutoff * len(autotune.SMALL_SORTS) * 3
+
+
+def test_reference_arm_runs_the_same_config(capsys):
+    import json
+    bench.main(["--impl", "reference", "--log2n", "14", "--steps", "2", "--warmup", "1"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    a = bench.parse_args(["--log2n", "14"])
+    assert line["impl"] == "reference" and line["config"] == bench.workload_config(a)
+    assert line["steps"] == 2 and len(line["step_seconds"]) == 2 and line["sorted_check"]
+    assert abs(line["ms_per_step"] - 1e3 * sum(line["step_seconds"]) / 2) < 1.0
+    assert line["value"] == line["cpu_baseline"]["value"] == line["e2e"]["value"]
+    assert line["cpu_baseline"]["cores"] == 1 and line["cpu_baseline"]["kind"] == "oracle"

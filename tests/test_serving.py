@@ -70,11 +70,11 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         torch.cuda.synchronize()
         assert torch.equal(r.result.view(torch.int64 if r.dtype != "int32" else torch.int32),
                            alone.view(torch.int64 if r.dtype != "int32" else torch.int32)), r.rid
-    for r in reqs[:5]:
+    for r in reqs:   # and every result is the oracle's sort of the request's keys
         want = oracle.sort(pool.keys(r).cpu().numpy())
         got = r.result.cpu().numpy()
-        assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
-    assert all(r.latency >= 0 for r in reqs)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), r.rid
+    assert all(r.latency >= 0 and r.queue_delay >= 0 for r in reqs)
 
 
 @pytest.mark.gpu
@@ -83,6 +83,11 @@ def test_plain_mode_serves_every_request():
     build.build()
     pool = serving.KeyPool(max_size=1 << 18, seed=4)
     reqs = serving.make_requests(20, rate_hz=5_000.0, seed=4, log2_lo=4.0, log2_hi=18.0)
-    rep = serving.ServingLoop(pool, mode="plain").run(reqs)
-    assert rep["requests"] == 20 and rep["batches"] == 20
+    loop = serving.ServingLoop(pool, mode="plain", keep_results=True)
+    rep = loop.run(reqs)
+    assert rep["requests"] == 20 and rep["batches"] == 20 and rep["slots"] == 3
     assert rep["p99_ms"] >= rep["p50_ms"] > 0
+    import oracle
+    for r in reqs:
+        want = oracle.sort(pool.keys(r).cpu().numpy())
+        assert np.array_equal(r.result.cpu().numpy().view(np.uint8), want.view(np.uint8)), r.rid
