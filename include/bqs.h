@@ -235,7 +235,7 @@ typedef enum {
                                stream waits for them before the call returns.  0 (the
                                default): everything on the caller's stream.  Used when
                                the host reads the counts after every level. */
-  BQS_OPT_LOCAL_SORT = 11   /* with BQS_OPT_LOCAL_CUTOFF on, key-only sorts and
+  BQS_OPT_LOCAL_SORT = 11,  /* with BQS_OPT_LOCAL_CUTOFF on, key-only sorts and
                                BQS_OPT_SMALL_SORT = 0: the block that partitions a
                                segment in shared memory also sorts up to this many of
                                its finished sub-segments there (the same warp-group
@@ -244,6 +244,19 @@ typedef enum {
                                the network kernels.  0 .. 128, default 0 (measured
                                slower: the block's load, partition and network phases
                                run one after another at 2 blocks per SM) */
+  BQS_OPT_COOP_MAX = 12     /* single-array key-only sorts (bqs_sort) of more than the
+                               small cutoff and at most this many keys run every level in
+                               one cooperative launch (all blocks resident, bounded grid-
+                               wide barriers between the phases of a level) instead of the
+                               host-driven level loop; the call then reads the control
+                               block back once, at its end.  0 = never (the default: at
+                               2^18..2^22 keys it measured no faster than the host loop,
+                               its grid-wide barriers waiting on the slowest block).
+                               Not used on a stream that is being captured, by
+                               bqs_sort_noalloc, with BQS_OPT_LEVEL_LOOP = 1,
+                               BQS_OPT_SMALL_SORT = 1 or local partitioning on, or when
+                               the device refuses the cooperative launch (the host loop
+                               runs instead). */
 } bqs_option;
 
 int bqs_set_option(int32_t opt, int64_t value);
@@ -276,6 +289,7 @@ typedef struct {
   int64_t kernel_launches;   /* kernels this library launched for the call */
   double partition_ms;       /* sum of timed partition launches (BQS_OPT_TIMING) */
   double partition_bytes;    /* algorithmic bytes of those launches */
+  double coop_ms;            /* the cooperative launch's duration (BQS_OPT_TIMING), else 0 */
 } bqs_stats;
 
 int bqs_get_stats(bqs_stats* out);

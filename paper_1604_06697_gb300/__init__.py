@@ -16,7 +16,7 @@ DTYPE_CODES = {"int32": 0, "int64": 1, "float64": 2}
 OPTIONS = {"pivot": 0, "small_cutoff": 1, "depth_limit": 2, "timing": 3, "tile": 4,
            "local_cutoff": 5, "wait_limit": 6, "test_stall": 7, "level_loop": 8,
            "small_sort": 9, "overlap": 10,
-           "local_sort": 11}
+           "local_sort": 11, "coop_max": 12}
 
 
 class BqsError(RuntimeError):

@@ -27,7 +27,7 @@ class Stats(ctypes.Structure):
         "levels", "partition_launches", "active_keys", "moved_keys", "equal_keys",
         "small_segments", "small_keys", "local_segments", "local_keys", "fallback_pivots",
         "kernel_launches")] + [
-        ("partition_ms", c_dbl), ("partition_bytes", c_dbl)]
+        ("partition_ms", c_dbl), ("partition_bytes", c_dbl), ("coop_ms", c_dbl)]
 
 
 # name -> (restype, argtypes); mirrors include/bqs.h

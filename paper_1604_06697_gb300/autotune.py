@@ -24,7 +24,8 @@ SMALL_CUTOFFS = (256, 1024, 2048, 4096)   # above 2048: key-only sorts, warp-gro
 LOCAL_CUTOFFS = (0, -1)        # off, or as large as one thread block holds
 SMALL_SORTS = (0, 1)           # warp / warp-group networks, or 256-thread block networks
 OVERLAPS = (0, 1)              # networks on the call's stream, or beside the partitions
-KNOBS = ("tile", "small_cutoff", "local_cutoff", "small_sort", "overlap")
+COOP_MAX = 1 << 22             # single arrays up to this size may run as one cooperative launch
+KNOBS = ("tile", "small_cutoff", "local_cutoff", "small_sort", "overlap", "coop_max")
 
 
 def default_cache_path() -> str:
@@ -35,7 +36,7 @@ def default_cache_path() -> str:
 def cache_key(dtype: str, n: int, kind: str) -> str:
     import torch
     gpu = torch.cuda.get_device_name()
-    return f"{gpu}|{dtype}|{kind}|2^{max(0, int(math.log2(max(1, n))))}"
+    return f"{gpu}|{dtype}|{kind}|2^{max(0, int(math.log2(max(1, n))))}|v2"
 
 
 def _load(path):
@@ -75,14 +76,19 @@ def _time(run, reps: int) -> float:
     return min(ms)
 
 
-def candidate_configs(kind: str = "sort") -> list:
+def candidate_configs(kind: str = "sort", n: int | None = None) -> list:
     """Every launch shape the tuner times for a workload kind.  Cutoffs above 2048 keys
     exist only for key-only sorts with the warp-group networks (the library clamps the
     others to 2048), so they are not timed twice."""
-    return [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o)
+    host = [dict(tile=t, small_cutoff=s, local_cutoff=l, small_sort=w, overlap=o, coop_max=0)
             for t, s, l, w, o in itertools.product(TILES, SMALL_CUTOFFS, LOCAL_CUTOFFS,
                                                    SMALL_SORTS, OVERLAPS)
             if s <= 2048 or (kind != "pairs" and w == 0)]
+    # Single arrays that fit the cooperative launch: every level in one kernel (tile,
+    # local partitioning and overlap do not apply there), one candidate per cutoff.
+    coop = [dict(tile=0, small_cutoff=s, local_cutoff=0, small_sort=0, overlap=0, coop_max=COOP_MAX)
+            for s in SMALL_CUTOFFS] if kind == "sort" and (n is None or n <= COOP_MAX) else []
+    return host + coop
 
 
 def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int | None = None,
@@ -145,7 +151,7 @@ def tune(dtype: str, n: int, kind: str = "sort", nseg: int = 0, reps: int | None
 
     saved = {k: bqs.get_option(k) for k in KNOBS}
     results = []
-    cands = candidates or candidate_configs(kind)
+    cands = candidates or candidate_configs(kind, n)
     try:
         for cfg in cands:
             apply(cfg)

@@ -297,6 +297,10 @@ int bqs_set_option(int32_t opt, int64_t value) {
       if (value < 0 || value > kLocalSortCap) return BQS_ERR_INVALID;
       g_opt.local_sort = value;
       return BQS_OK;
+    case BQS_OPT_COOP_MAX:
+      if (value < 0 || value > kMaxN) return BQS_ERR_INVALID;
+      g_opt.coop_max = value;
+      return BQS_OK;
     default:
       return BQS_ERR_UNSUPPORTED;
   }
@@ -318,6 +322,7 @@ int bqs_get_option(int32_t opt, int64_t* value) {
     case BQS_OPT_SMALL_SORT: *value = g_opt.small_sort; return BQS_OK;
     case BQS_OPT_OVERLAP: *value = g_opt.overlap; return BQS_OK;
     case BQS_OPT_LOCAL_SORT: *value = g_opt.local_sort; return BQS_OK;
+    case BQS_OPT_COOP_MAX: *value = g_opt.coop_max; return BQS_OK;
     default: return BQS_ERR_UNSUPPORTED;
   }
 }
@@ -356,6 +361,7 @@ int bqs_get_stats(bqs_stats* out) {
   out->kernel_launches = s.kernel_launches;
   out->partition_ms = s.partition_ms;
   out->partition_bytes = (double)(s.active_keys + s.moved_keys) * s.partition_bytes_per_key;
+  out->coop_ms = s.coop_ms;
   return BQS_OK;
 }
 

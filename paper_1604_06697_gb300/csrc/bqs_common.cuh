@@ -115,6 +115,9 @@ struct Ctrl {
   unsigned long long active_total;  // sum of partitioned keys over those levels
   unsigned long long local_runs;    // segments partitioned by one block in shared memory
   unsigned long long small_runs;    // segments finished by the sorting networks
+  // grid-wide barrier of the cooperative single-launch sort
+  unsigned int bar_count;           // blocks arrived at the current barrier
+  unsigned int bar_gen;             // barriers completed
 };
 
 struct Bufs {

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bqs_coop.cuh"
 #include "bqs_graph.cuh"
 #include "bqs_internal.h"
 #include "bqs_kernels.cuh"
@@ -505,6 +506,69 @@ int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_level
   return kOk;
 }
 
+// The single-launch sort (bqs_coop.cuh): one cooperative launch over a persistent grid,
+// then one read-back of the control block.  Returns kCoopRefused (nothing enqueued)
+// when the device cannot make every block resident; the caller then runs the host loop.
+constexpr int kCoopRefused = 1;
+
+template <class KT>
+int run_coop(Params P, int64_t n, int max_levels, bool timing, int test_stall, cudaStream_t s,
+             Ctrl* host, bool host_mapped, Stats& st) {
+  const void* fn = (const void*)k_coop_sort<KT>;
+  const int grid = persistent_grid(fn, kCoopThreads, CoopShape<KT>::smem);
+  int coop = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return kCoopRefused;
+  }
+  P.local_cutoff = P.small_cutoff;   // no single-block local partitioning here
+  P.tile = CoopShape<KT>::TILE;      // the tile space of this kernel's partition step
+  P.test_stall = test_stall;
+  P.device_loop = 0;
+  void* args[] = {(void*)&P, (void*)&n, (void*)&max_levels};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timing) {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs = timing_events();
+    if (evs.empty()) {
+      cudaEvent_t a, b;
+      BQS_CK(cudaEventCreate(&a));
+      BQS_CK(cudaEventCreate(&b));
+      evs.emplace_back(a, b);
+    }
+    e0 = evs[0].first;
+    e1 = evs[0].second;
+    BQS_CK(cudaEventRecord(e0, s));
+  }
+  const cudaError_t le = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args,
+                                                     CoopShape<KT>::smem, s);
+  if (le == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return kCoopRefused;
+  }
+  if (le != cudaSuccess) return fail_cuda(le, "cudaLaunchCooperativeKernel(k_coop_sort)");
+  if (timing) BQS_CK(cudaEventRecord(e1, s));
+  BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
+  BQS_CK(cudaStreamSynchronize(s));
+  if (host->status) return status_code(host->status);
+  st.kernel_launches += 2;   // the sort and the control-block read-back
+  st.levels = (int64_t)host->levels_run;
+  st.partition_launches = 0;
+  st.active_keys = (int64_t)host->active_total;
+  st.moved_keys = (int64_t)host->moved_keys;
+  st.equal_keys = (int64_t)host->equal_keys;
+  st.small_keys = (int64_t)host->small_keys;
+  st.small_segments = (int64_t)host->small_runs;
+  st.fallback_pivots = (int64_t)host->fallbacks;
+  st.partition_bytes_per_key = (double)sizeof(typename KT::U);
+  if (timing) {
+    float ms = 0;
+    BQS_CK(cudaEventElapsedTime(&ms, e0, e1));
+    st.coop_ms = ms;
+  }
+  return kOk;
+}
+
 template <class KT, bool PAIRS>
 int run_call(const Call& c, Stats& st) {
   using U = typename KT::U;
@@ -602,6 +666,17 @@ int run_call(const Call& c, Stats& st) {
   Ctrl* host = (c.fixed_ws || device_loop) ? &pageable_ctrl : pinned_ctrl(&host_mapped);
   const bool timing = c.opt.timing && !c.fixed_ws && !device_loop;
   BQS_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), s));
+
+  if constexpr (!PAIRS) {
+    // Single arrays of up to BQS_OPT_COOP_MAX keys: every level in one launch.
+    if (!device_loop && !c.fixed_ws && !c.partition_only && !c.seg_offsets &&
+        c.opt.level_loop == 0 && c.opt.small_sort == 0 && local_cutoff <= small_cutoff &&
+        c.n > small_cutoff && c.n <= c.opt.coop_max) {
+      const int rc_coop = run_coop<KT>(P, c.n, P.depth_limit + 8 * (int)sizeof(U) + 40, timing,
+                                       c.opt.test_stall ? 1 : 0, s, host, host_mapped, st);
+      if (rc_coop != kCoopRefused) return rc_coop;
+    }
+  }
 
   ListCounts cur{};
   bool host_fresh = false;   // `host` holds this call's control block

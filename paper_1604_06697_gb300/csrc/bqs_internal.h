@@ -33,6 +33,7 @@ struct Options {
   int64_t small_sort = 0;      // 1: 256-thread block networks for every small segment
   int64_t overlap = 0;         // 1: sorting networks on a second stream, beside the partitions
   int64_t local_sort = 0;      // leaves per segment the single-block local partitioning sorts
+  int64_t coop_max = 0;        // single arrays up to this size: one cooperative launch (0: off)
 };
 
 struct Call {
@@ -58,6 +59,7 @@ struct Stats {
   int64_t small_segments = 0, small_keys = 0, local_segments = 0, local_keys = 0;
   int64_t fallback_pivots = 0, kernel_launches = 0;
   double partition_ms = 0, partition_bytes_per_key = 0;
+  double coop_ms = 0;   // duration of the cooperative launch (BQS_OPT_TIMING)
 };
 
 // Implemented in bqs_api.cu.

@@ -302,20 +302,33 @@ __global__ void __launch_bounds__(256) k_init_segments(Params P, const int64_t* 
 //    range when all its keys are equal): each such level halves the range, so the
 //    recursion depth stays bounded by the key width (the role Heapsort plays in Sec. 2).
 // All other pivots are chosen by route_warp when the segment is created.
+// Shared memory of the pivot pass (one 256-thread block).
 template <class KT, bool PAIRS>
-__global__ void __launch_bounds__(256) k_pivot(Params P) {
+struct PivotSmem {
+  static constexpr int kBlockList = 64;
+  alignas(16) typename KT::U k[512];            // staging rows of the sample sort
+  alignas(16) uint32_t v[PAIRS ? 512 : 1];
+  typename KT::U red[2][8];
+  uint32_t redv[2][8];
+  unsigned int blk[kBlockList];                 // segments this block's warps leave to it
+  int nblk;
+};
+
+// The pivot pass over the `todo` list of parity pp, by every 256-thread block of the
+// grid (k_pivot, and one step of the cooperative sort).
+template <class KT, bool PAIRS>
+__device__ void pivot_pass(const Params& P, int pp, PivotSmem<KT, PAIRS>& sm) {
   using U = typename KT::U;
   using E = Elem<KT, PAIRS>;
   static_assert(kMaxSample < 512, "two sample entries per thread of 256");
-  __shared__ __align__(16) U s_k[512];                   // staging rows of the sample sort
-  __shared__ __align__(16) uint32_t s_v[PAIRS ? 512 : 1];
-  __shared__ U s_red[2][8];
-  __shared__ uint32_t s_redv[2][8];
-  constexpr int kBlockList = 64;
-  __shared__ unsigned int s_blk[kBlockList];   // segments this block's warps leave to it
-  __shared__ int s_nblk;
+  U* s_k = sm.k;
+  uint32_t* s_v = sm.v;
+  auto& s_red = sm.red;
+  auto& s_redv = sm.redv;
+  constexpr int kBlockList = PivotSmem<KT, PAIRS>::kBlockList;
+  unsigned int* s_blk = sm.blk;
+  int& s_nblk = sm.nblk;
 
-  const int pp = level_parity(P, P.p);
   const unsigned int count = min(P.ctrl->lists[pp].todo, P.l.cap_large);
   Seg* segs = P.l.large[pp];
   auto sample_size = [](int64_t len) {
@@ -474,6 +487,12 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
     }
     __syncthreads();
   }
+}
+
+template <class KT, bool PAIRS>
+__global__ void __launch_bounds__(256) k_pivot(Params P) {
+  __shared__ PivotSmem<KT, PAIRS> sm;
+  pivot_pass<KT, PAIRS>(P, level_parity(P, P.p), sm);
 }
 
 // ---- children of the partitioned segments ------------------------------------------------

@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
       uint32_t* vr = vdst + right;
       for (uint32_t j = tid; j < ngt; j += THREADS) vr[j] = s_vout[nlt + j];
     }
-    __syncthreads();   // s_out, s_wcnt and s_base are reused by the next tile
+    // No barrier here: the next tile's first barrier (after its mbarrier wait) orders
+    // every reuse of s_out, s_wcnt and s_base after this write-out, and the descriptor
+    // slot that a lookup at the next tile may refill belongs to a finished chunk.
   }
   if (s_abort && tid == 0) {
     // Let the copies already issued (tiles i .. i+STAGES-1) land before the block's

@@ -31,6 +31,14 @@ def test_autotune_candidates_cover_every_knob_once():
         keys = [tuple(sorted(c.items())) for c in cands]
         assert len(keys) == len(set(keys))                       # no duplicates
         assert all(set(c) == set(autotune.KNOBS) for c in cands)
+        coop = [c for c in cands if c["coop_max"]]
+        # the single-launch path: single arrays only, one candidate per cutoff, with
+        # the settings it needs (no local partitioning, warp-group networks)
+        assert len(coop) == (len(autotune.SMALL_CUTOFFS) if kind == "sort" else 0)
+        assert all(c["small_sort"] == 0 and c["local_cutoff"] == 0 for c in coop)
+        assert autotune.candidate_configs(kind, n=autotune.COOP_MAX + 1) == \
+            [c for c in cands if not c["coop_max"]]
+        cands = [c for c in cands if not c["coop_max"]]
         for c in cands:                                          # 4096 only where it applies
             if c["small_cutoff"] > 2048:
                 assert kind != "pairs" and c["small_sort"] == 0

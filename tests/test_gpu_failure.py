@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault.
 
-The partition kernel's waits on its shared-memory pipeline are bounded.  A test-only
+The partition kernel's waits on its shared-memory pipeline and the grid-wide barriers
+of the single-launch sort are bounded.  A test-only
 option leaves one tile unrequested, so that wait runs out: the kernel records a
 timeout in the device status word, waits (again bounded) for the copies it did
 issue, and returns.  The call reports BQS_ERR_TIMEOUT and the device stays usable:
@@ -50,3 +51,31 @@ def test_bounded_wait_times_out_and_device_stays_usable(bqs, level_loop, overlap
     bqs.sort(t2)
     torch.cuda.synchronize()
     assert np.array_equal(t2.cpu().numpy(), oracle.sort(a))
+
+
+def test_single_launch_barrier_times_out_and_device_stays_usable(bqs):
+    # The single-launch sort meets at grid-wide barriers; the test option keeps block 0
+    # from arriving at the first one, so every other block's bounded wait runs out and
+    # records the timeout.  The call reports BQS_ERR_TIMEOUT and the next sort (the
+    # same path) is correct.
+    import torch
+    a = inputs.make_keys(1 << 20, "int32", "uniform", seed=9)
+    t = torch.from_numpy(a).cuda()
+    old = {k: bqs.get_option(k) for k in ("coop_max", "wait_limit")}
+    bqs.set_option("coop_max", 1 << 22)
+    bqs.set_option("wait_limit", 1 << 16)
+    bqs.set_option("test_stall", 1)
+    try:
+        with pytest.raises(bqs.BqsError) as e:
+            bqs.sort(t)
+        assert e.value.status == -4
+    finally:
+        bqs.set_option("test_stall", 0)
+        bqs.set_option("wait_limit", old["wait_limit"])
+    torch.cuda.synchronize()
+    t2 = torch.from_numpy(a).cuda()
+    bqs.sort(t2)
+    torch.cuda.synchronize()
+    assert bqs.stats()["partition_launches"] == 0          # the single launch ran again
+    assert np.array_equal(t2.cpu().numpy(), oracle.sort(a))
+    bqs.set_option("coop_max", old["coop_max"])

@@ -36,6 +36,14 @@ def assert_same_bits(got, want):
     assert got.shape == want.shape and np.array_equal(gu, wu)
 
 
+@pytest.fixture(autouse=True)
+def host_driven_loops(bqs):
+    # Both loops under test are host-driven; arrays up to BQS_OPT_COOP_MAX keys would
+    # otherwise take the single-launch path with level_loop 0 (test_gpu_coop.py).
+    bqs.set_option("coop_max", 0)
+    yield
+
+
 def sort_with(bqs, a, loop):
     import torch
     bqs.set_option("level_loop", loop)

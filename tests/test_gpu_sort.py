@@ -30,7 +30,10 @@ def bqs():
 
 @pytest.fixture(autouse=True)
 def default_options(bqs):
+    # These tests check the host-driven level loop at every size; the single-launch
+    # path for arrays up to BQS_OPT_COOP_MAX keys has its own (test_gpu_coop.py).
     saved = {k: bqs.get_option(k) for k in bqs.OPTIONS}
+    bqs.set_option("coop_max", 0)
     yield
     for k, v in saved.items():
         bqs.set_option(k, v)
