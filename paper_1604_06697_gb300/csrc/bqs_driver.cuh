@@ -895,7 +895,10 @@ int run_call(const Call& c, Stats& st) {
   }
   st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
   if (timing && ev_used) {
-    BQS_CK(cudaStreamSynchronize(s));
+    // The partition launches are in stream order, so the last one's end event is the
+    // last to complete; waiting for it (not for the whole stream) lets the call return
+    // while the last level's networks still run, as an untimed call does.
+    BQS_CK(cudaEventSynchronize(evs[ev_used - 1].second));
     double ms = 0;
     for (size_t i = 0; i < ev_used; ++i) {
       float t = 0;

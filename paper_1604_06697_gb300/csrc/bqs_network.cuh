@@ -406,6 +406,156 @@ __device__ __forceinline__ void net_sort_transposed(uint32_t (&x)[32], int t, ui
   }
 }
 
+// ---- the flip form of the network, with padding skipped (32-bit keys, R = 32) -----------
+//
+// Every merge phase k of Batcher's network can start with a "flip" stage, which pairs
+// entry e with e ^ (k - 1) inside its block of k entries, and continue with half-
+// cleaners (e with e ^ j, j = k/4 .. 1).  All comparators are then ascending (the lower
+// entry keeps the minimum) and, after every phase, every block of k entries is sorted
+// ascending.  So padding with the largest key, placed at the top (entries len and up),
+// stays where it is through the whole network: every comparator that touches an entry
+// at or above len leaves both entries as they are.  A warp whose 32 x 32 entries all lie
+// at or above len therefore has nothing to do, and the warps below it never need its
+// entries.  Only the first ceil(len / 1024) warps of the group work; they synchronise
+// among themselves on named barrier 1.  No entry is ever complemented.
+
+// Barrier of the `act` working warps (named barrier 1; a single warp needs none).
+__device__ __forceinline__ void sync_active(int act) {
+  if (act == 1) __syncwarp();
+  else asm volatile("bar.sync 1, %0;" ::"r"(act * 32) : "memory");
+}
+
+// Register half-cleaners J, J/2, ..., 1 (entry bits of the register index).
+template <int J>
+__device__ __forceinline__ void hc_regs32(uint32_t (&x)[32]) {
+  if constexpr (J >= 1) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if ((i & J) == 0) {
+        const uint32_t lo = umin_(x[i], x[i | J]), hi = umax_(x[i], x[i | J]);
+        x[i] = lo;
+        x[i | J] = hi;
+      }
+    hc_regs32<J / 2>(x);
+  }
+}
+
+// Phases 2 .. 32 on a thread's own 32 entries: flip stage, then half-cleaners.
+template <int K>
+__device__ __forceinline__ void flip_phases_regs32(uint32_t (&x)[32]) {
+  if constexpr (K <= 32) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if ((i & (K / 2)) == 0) {
+        const int u = i ^ (K - 1);
+        const uint32_t lo = umin_(x[i], x[u]), hi = umax_(x[i], x[u]);
+        x[i] = lo;
+        x[u] = hi;
+      }
+    hc_regs32<K / 4>(x);
+    flip_phases_regs32<K * 2>(x);
+  }
+}
+
+// Half-cleaners of a transposed block on register bits nb-1 .. 0 (nb in 1..5).
+__device__ __forceinline__ void transposed_hc32(uint32_t (&x)[32], int nb) {
+  switch (nb) {
+    case 5: hc_regs32<16>(x); break;
+    case 4: hc_regs32<8>(x); break;
+    case 3: hc_regs32<4>(x); break;
+    case 2: hc_regs32<2>(x); break;
+    default: hc_regs32<1>(x);
+  }
+}
+
+// Compare-exchange of a thread's 32 entries with the staged row pt of its partner
+// thread, 16 bytes at a time (at most four partner entries live): entry i meets the
+// partner's entry i, or 31 - i when REV (a flip stage); the lower thread keeps minima.
+template <bool REV>
+__device__ __forceinline__ void cx_with_row32(uint32_t (&x)[32], const uint32_t* s_x, int pt,
+                                              bool lower) {
+  using S = RowSwizzle<uint32_t, 32>;
+  const int kq = S::key(pt);
+#pragma unroll
+  for (int c = 0; c < S::C; ++c) {
+    const uint4 v = reinterpret_cast<const uint4*>(s_x)[pt * (S::STRIDE / S::EPC) + (c ^ kq)];
+    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = REV ? 31 - (c * 4 + w) : c * 4 + w;
+      x[i] = lower ? umin_(x[i], e[w]) : umax_(x[i], e[w]);
+    }
+  }
+}
+
+// Sorts M = 32 * T entries (entry e = t * 32 + i in register i of network thread t,
+// padded with 0xFFFFFFFF from entry len on) ascending.  Only network threads of the
+// first `act` = ceil(len / 1024) warps call it; s_x holds the group's staging rows
+// (row t for network thread t), wb the 32 rows of the calling warp.
+template <int T>
+__device__ __forceinline__ void net_sort_flip32(uint32_t (&x)[32], int t, uint32_t* s_x, int act) {
+  constexpr int R = 32, M = R * T;
+  const int lane = t & 31;
+  uint32_t* wb = s_x + (t >> 5) * 32 * RowSwizzle<uint32_t, 32>::STRIDE;
+  // Lane half-cleaners j .. R of a phase (j <= 16 R): a shuffle for one stage, a warp
+  // transpose around register stages for more.
+  auto lane_hc = [&](int j) {
+    if (j == R) {
+      const bool lower = (lane & 1) == 0;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const uint32_t p = __shfl_xor_sync(~0u, x[i], 1);
+        x[i] = lower ? umin_(x[i], p) : umax_(x[i], p);
+      }
+    } else if (j > R) {
+      warp_transpose32(x, lane, wb);
+      transposed_hc32(x, 31 - __clz(j / R) + 1);
+      warp_transpose32(x, lane, wb);
+    }
+  };
+  flip_phases_regs32<2>(x);                                     // phases 2 .. 32
+  // Phases 64 .. 1024, inside each warp: the flip pairs lane ^ m, register 31 - i, and
+  // the lane whose entries are in the lower half of the block keeps the minimum.
+#pragma unroll 1
+  for (int k = 2 * R; k <= M && k <= 32 * R; k <<= 1) {
+    const int m = k / R - 1;
+    const bool lower = (lane & ((m + 1) >> 1)) == 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t a = __shfl_xor_sync(~0u, x[31 - i], m);
+      const uint32_t b = __shfl_xor_sync(~0u, x[i], m);
+      x[i] = lower ? umin_(x[i], a) : umax_(x[i], a);
+      x[31 - i] = lower ? umin_(x[31 - i], b) : umax_(x[31 - i], b);
+    }
+    lane_hc(k >> 2);
+    hc_regs32<16>(x);
+  }
+  // Phases 2048 .. M, across warps: the flip and the half-cleaners between warps go
+  // through the staging rows (the flip reads the partner's row backwards).  The rows of
+  // warps without data hold padding from the load, so a partner there changes nothing.
+#pragma unroll 1
+  for (int k = 64 * R; k <= M; k <<= 1) {
+    int d = k / R - 1;
+    bool rev = true;
+#pragma unroll 1
+    for (int j = k >> 1; j >= 32 * R; j >>= 1) {
+      const int pt = t ^ d;
+      const bool lower = (t & (j / R)) == 0;
+      swz_store_row<R>(s_x, t, x);
+      sync_active(act);
+      if ((pt >> 5) < act) {
+        if (rev) cx_with_row32<true>(x, s_x, pt, lower);
+        else cx_with_row32<false>(x, s_x, pt, lower);
+      }
+      sync_active(act);
+      d = (j >> 1) / R;
+      rev = false;
+    }
+    lane_hc(16 * R);
+    hc_regs32<16>(x);
+  }
+}
+
 // 64-bit keys, R = 16: entry bits 0..3 are register bits and 4..8 lane bits.  Each
 // half warp transposes its 16 x 16 block (register i of lane l <-> register l of lane
 // i within the half), which brings entry bits 4..7 into the registers; bit 8 (lane

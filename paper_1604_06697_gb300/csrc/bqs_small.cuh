@@ -108,12 +108,42 @@ struct SmallGroup {   // the block that sorts segments above small_warp_max()
 // Sorts len <= R*T raw keys from src (global or shared memory) into dst (the final
 // buffer) with T threads; sw: their staging rows.  NB: the T threads are one of several
 // groups of the block (named barriers).
+// rot (flip form only): the group's warps take the network's warps rotated by rot, so
+// the warp that a short segment leaves idle changes from segment to segment (and with
+// it the sub-partition of the SM that waits).
 template <class KT, int R, int T, bool NB = false>
 __device__ __forceinline__ void group_sort_keys(const typename KT::U* src, typename KT::U* dst,
-                                                int len, int t, typename KT::U* sw) {
+                                                int len, int t, typename KT::U* sw, int rot = 0) {
   using U = typename KT::U;
   using S = RowSwizzle<U, R>;
   auto sync = [] { sync_group<T, NB>(); };
+  if constexpr (sizeof(U) == 4 && R == 32 && !NB && T > 32) {
+    // The flip form of the network: only the first ceil(len / 1024) network warps hold
+    // entries below len, and only they run the network (the rows of the others stay
+    // padding).  Every thread still takes part in the coalesced loads and stores.
+    const int act = min(T / 32, (len + 32 * R - 1) / (32 * R));
+    const int tn = (t + rot * 32) & (T - 1);   // network thread index
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int e = i * T + t;
+      sw[S::pos(e)] = e < len ? KT::ord(src[e]) : ~U(0);
+    }
+    sync();
+    if ((tn >> 5) < act) {
+      U x[R];
+      swz_load_row<R>(sw, tn, x);
+      net_sort_flip32<T>(x, tn, sw, act);
+      swz_store_row<R>(sw, tn, x);
+    }
+    sync();
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int e = i * T + t;
+      if (e < len) dst[e] = KT::unord(sw[S::pos(e)]);
+    }
+    sync();
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int e = i * T + t;
@@ -140,10 +170,10 @@ __device__ __forceinline__ void group_sort_keys(const typename KT::U* src, typen
 
 template <class KT, int R, int T>
 __device__ __forceinline__ void group_sort_run(const Params& P, const Run& r, int t,
-                                               typename KT::U* sw) {
+                                               typename KT::U* sw, int rot = 0) {
   using U = typename KT::U;
   group_sort_keys<KT, R, T>((const U*)P.b.key[r.parity] + r.off, (U*)P.b.final_key + r.off,
-                            (int)r.len, t, sw);
+                            (int)r.len, t, sw, rot);
 }
 
 // Key-only small segments of kWarpSortMax+1 .. small_warp_max() keys (list `small`),
@@ -193,8 +223,8 @@ __global__ void __launch_bounds__(SmallGroup<KT>::TBIG, SmallGroup<KT>::BLOCKS_B
   p = level_parity(P, p);
   __shared__ __align__(16) U s_x[staging_entries<U, G::RMAX, G::TBIG>()];
   const unsigned int count = min(P.fixed_counts ? P.n_big : P.ctrl->lists[p].big, P.l.cap_run);
-  for (unsigned int s = blockIdx.x; s < count; s += gridDim.x)
-    group_sort_run<KT, G::RMAX, G::TBIG>(P, P.l.big[p][s], threadIdx.x, s_x);
+  for (unsigned int s = blockIdx.x, k = 0; s < count; s += gridDim.x, ++k)
+    group_sort_run<KT, G::RMAX, G::TBIG>(P, P.l.big[p][s], threadIdx.x, s_x, (int)((blockIdx.x + k) & 3));
 }
 
 // ---- key-value segments as packed 64-bit keys ------------------------------------------

@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
       // (needed once the refills run STAGES tiles ahead into it).
       lookup_chunk(i / CHUNK + 1);
     }
-    if (!mbar_wait_bounded(&s_bar[st], parity, P.ctrl, P.wait_limit)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) break;
+    // Every thread waits for the tile itself (the mbarrier's acquire makes the bulk copy
+    // visible to it); a wait that gave up is acted on at the first block barrier below,
+    // which every thread reaches, so the whole block leaves the loop together.
+    const bool waited = mbar_wait_bounded(&s_bar[st], parity, P.ctrl, P.wait_limit);
 
     const TileInfo ti = s_info[((i / CHUNK) & 1) * CHUNK + (i % CHUNK)];
     const int64_t abase = tile_origin(ti.off) + (int64_t)(ti.parity >> 1) * TILE;
@@ -276,7 +277,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
       if (lane >= o) incl += y;
     }
     if (lane == 31) s_wcnt[warp] = incl;
-    __syncthreads();
+    // This barrier also orders the reuse of s_out, s_wcnt and s_base after the previous
+    // tile's write-out (no thread stages before every thread is past that write-out).
+    if (__syncthreads_or(!waited)) {
+      if (tid == 0) s_abort = 1;
+      break;
+    }
     uint32_t off_lt = 0, off_gt = 0, nlt = 0, ngt = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) {
@@ -335,9 +341,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
       uint32_t* vr = vdst + right;
       for (uint32_t j = tid; j < ngt; j += THREADS) vr[j] = s_vout[nlt + j];
     }
-    // No barrier here: the next tile's first barrier (after its mbarrier wait) orders
-    // every reuse of s_out, s_wcnt and s_base after this write-out, and the descriptor
-    // slot that a lookup at the next tile may refill belongs to a finished chunk.
+    // No barrier here: the next tile's first barrier orders every reuse of s_out, s_wcnt
+    // and s_base after this write-out, and the descriptor slot that a lookup at the next
+    // tile may refill belongs to a finished chunk.
   }
   if (s_abort && tid == 0) {
     // Let the copies already issued (tiles i .. i+STAGES-1) land before the block's
