@@ -201,7 +201,11 @@ typedef enum {
   BQS_OPT_SMALL_CUTOFF = 1, /* small-segment cutoff C, 2 .. 4096 (default 2048); key-value
                                sorts and BQS_OPT_SMALL_SORT = 1 use at most 2048 */
   BQS_OPT_DEPTH_LIMIT = 2,  /* < 0: 2*floor(log2 n)+3 (default); else this level count */
-  BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events (stats) */
+  BQS_OPT_TIMING = 3,       /* 1: time every partition launch with CUDA events; the call
+                               waits for its last one and reports the sum in partition_ms;
+                               2 (sorts of the host-driven loop): the same events, but
+                               the call never waits for them; bqs_timing_collect() sums
+                               them later (partition_ms of the call stays 0) */
   BQS_OPT_TILE = 4,         /* partition tile variant: 0 = default, 1..N autotuner choices */
   BQS_OPT_LOCAL_CUTOFF = 5, /* segments up to this size are partitioned down to the small
                                cutoff inside one thread block's shared memory (one HBM
@@ -293,6 +297,15 @@ typedef struct {
 } bqs_stats;
 
 int bqs_get_stats(bqs_stats* out);
+
+/*
+ * bqs_timing_collect -- with BQS_OPT_TIMING = 2, the summed duration (ms) of the
+ * partition launches that had work in the calling thread's sorts on the current device
+ * since the last collect, and how many there were.  Waits for those launches to end
+ * (call it after synchronising the streams the sorts ran on).  Either pointer may be
+ * NULL.
+ */
+int bqs_timing_collect(double* ms, int64_t* launches);
 
 /* Static description of a status code (thread-local detail for BQS_ERR_CUDA). */
 const char* bqs_status_string(int status);

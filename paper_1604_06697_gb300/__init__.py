@@ -196,3 +196,11 @@ def stats() -> dict:
     s = _native.Stats()
     _check(_native.lib().bqs_get_stats(ctypes.byref(s)), "bqs_get_stats")
     return {name: getattr(s, name) for name, _ in _native.Stats._fields_}
+
+
+def collect_timing():
+    """With the "timing" option at 2: (ms, launches) summed over the partition launches
+    that had work in this thread's sorts since the last collect (waits for them)."""
+    ms, n = ctypes.c_double(0), ctypes.c_int64(0)
+    _check(_native.lib().bqs_timing_collect(ctypes.byref(ms), ctypes.byref(n)), "bqs_timing_collect")
+    return float(ms.value), int(n.value)

@@ -44,6 +44,7 @@ SIGNATURES = {
     "bqs_workspace_bytes": (ctypes.c_int, [c_i64, c_i32, c_i32, c_i64, ctypes.POINTER(c_i64)]),
     "bqs_set_workspace": (ctypes.c_int, [c_vp, c_i64]),
     "bqs_get_stats": (ctypes.c_int, [ctypes.POINTER(Stats)]),
+    "bqs_timing_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_i64)]),
     "bqs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -116,7 +116,7 @@ std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() {
 }
 
 thread_local cudaStream_t t_side_stream[kMaxDevices];
-thread_local cudaEvent_t t_side_events[kMaxDevices][2];
+thread_local cudaEvent_t t_side_events[kMaxDevices][3];
 
 cudaStream_t side_stream() {
   cudaStream_t& s = t_side_stream[current_device_slot()];
@@ -128,12 +128,45 @@ cudaStream_t side_stream() {
 }
 
 cudaEvent_t side_event(int i) {
-  cudaEvent_t& e = t_side_events[current_device_slot()][i & 1];
+  cudaEvent_t& e = t_side_events[current_device_slot()][i % 3];
   if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     e = nullptr;
   }
   return e;
+}
+
+// Deferred partition timing (BQS_OPT_TIMING = 2): event pairs of finished calls wait in
+// `pending` until bqs_timing_collect; collected pairs return to `spare`.
+struct DeferredTiming {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare, pending;
+  std::vector<char> work;
+};
+thread_local DeferredTiming t_deferred[kMaxDevices];
+
+int deferred_event_pair(cudaEvent_t* e0, cudaEvent_t* e1) {
+  DeferredTiming& d = t_deferred[current_device_slot()];
+  if (d.spare.empty()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      return fail_cuda(e, "cudaEventCreate");
+    }
+    d.spare.emplace_back(a, b);
+  }
+  *e0 = d.spare.back().first;
+  *e1 = d.spare.back().second;
+  d.spare.pop_back();
+  return kOk;
+}
+
+void deferred_timing_push(cudaEvent_t e0, cudaEvent_t e1, bool work) {
+  DeferredTiming& d = t_deferred[current_device_slot()];
+  d.pending.emplace_back(e0, e1);
+  d.work.push_back(work ? 1 : 0);
 }
 
 cudaEvent_t counts_event() {
@@ -262,7 +295,7 @@ int bqs_set_option(int32_t opt, int64_t value) {
       g_opt.depth_limit = value;
       return BQS_OK;
     case BQS_OPT_TIMING:
-      if (value < 0 || value > 1) return BQS_ERR_INVALID;
+      if (value < 0 || value > 2) return BQS_ERR_INVALID;
       g_opt.timing = value;
       return BQS_OK;
     case BQS_OPT_TILE:
@@ -363,6 +396,29 @@ int bqs_get_stats(bqs_stats* out) {
   out->partition_bytes = (double)(s.active_keys + s.moved_keys) * s.partition_bytes_per_key;
   out->coop_ms = s.coop_ms;
   return BQS_OK;
+}
+
+int bqs_timing_collect(double* ms, int64_t* launches) {
+  DeferredTiming& d = t_deferred[current_device_slot()];
+  double total = 0;
+  int64_t count = 0;
+  int rc = BQS_OK;
+  for (size_t i = 0; i < d.pending.size(); ++i) {
+    if (rc == BQS_OK && d.work[i]) {
+      cudaError_t e = cudaEventSynchronize(d.pending[i].second);
+      float t = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, d.pending[i].first, d.pending[i].second);
+      if (e != cudaSuccess) rc = fail_cuda(e, "collecting partition timing");
+      total += t;
+      ++count;
+    }
+    d.spare.push_back(d.pending[i]);
+  }
+  d.pending.clear();
+  d.work.clear();
+  if (ms) *ms = total;
+  if (launches) *launches = count;
+  return rc;
 }
 
 const char* bqs_status_string(int status) {

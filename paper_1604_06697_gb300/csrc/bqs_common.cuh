@@ -163,6 +163,7 @@ struct Params {
   // device-side counts of their lists may already be cleared for the next level).
   int fixed_counts;
   uint32_t n_tiny, n_small, n_group, n_big;
+  unsigned long long n_fill;   // fill list (count | tiles << 32) for k_fill
 };
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {

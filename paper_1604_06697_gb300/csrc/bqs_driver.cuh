@@ -751,6 +751,198 @@ int run_call(const Call& c, Stats& st) {
   // partitions and the allocation-free entry point (which creates no CUDA objects)
   // synchronise the stream at the end of each level instead.
   const cudaEvent_t counts_ev = (c.partition_only || c.fixed_ws) ? nullptr : counts_event();
+
+  if (counts_ev && !c.partition_only) {
+    // ---- the level loop with one level of lookahead ----------------------------------
+    // The pivot pass and the partition kernel read their work counts from the control
+    // block, so level L+1's are enqueued (fixed grids) right after level L's bookkeeping
+    // and count read-back, before the host waits for those counts: the device never
+    // idles while the host turns around.  Networks (of the lists of parity p, written by
+    // the previous bookkeeping) run beside the partitions on a second stream with
+    // BQS_OPT_OVERLAP; `done[p]` marks their end, which the bookkeeping that rewrites the
+    // runs of parity p (two levels on) waits for.
+    cudaStream_t s1 = nullptr;
+    cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
+    if (c.opt.overlap) {
+      s1 = side_stream();
+      ready = side_event(0);
+      done[0] = side_event(1);
+      done[1] = side_event(2);
+      if (!s1 || !ready || !done[0] || !done[1]) s1 = nullptr;
+    }
+    bool side_work[2] = {false, false};
+    auto join = [&]() {
+      for (int k = 0; k < 2; ++k)
+        if (side_work[k]) cudaStreamWaitEvent(s, done[k], 0);
+    };
+    struct Join {
+      decltype(join)& f;
+      ~Join() { f(); }
+    } join_on_exit{join};
+    std::vector<char> timed_work;   // per timed partition launch: whether it had tiles
+    // BQS_OPT_TIMING = 2: each launch gets its own event pair, handed over at the end of
+    // the call for bqs_timing_collect, and the call never waits for them.
+    const bool deferred = timing && c.opt.timing == 2;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> call_evs;
+    auto launch_partition = [&](int p, int grid, int stall) -> int {
+      P.p = p;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (deferred) {
+        const int erc = deferred_event_pair(&e0, &e1);
+        if (erc) return erc;
+        call_evs.emplace_back(e0, e1);
+        BQS_CK(cudaEventRecord(e0, s));
+      } else if (timing) {
+        if (ev_used == evs.size()) {
+          cudaEvent_t a, b;
+          BQS_CK(cudaEventCreate(&a));
+          BQS_CK(cudaEventCreate(&b));
+          evs.emplace_back(a, b);
+        }
+        e0 = evs[ev_used].first;
+        e1 = evs[ev_used].second;
+        ++ev_used;
+        BQS_CK(cudaEventRecord(e0, s));
+      }
+      P.test_stall = stall;
+      var.launch(P, grid, s);
+      P.test_stall = 0;
+      if (timing) BQS_CK(cudaEventRecord(e1, s));
+      st.kernel_launches += 1;
+      return kOk;
+    };
+    // Every way out of the call hands the deferred pairs over (their recorded launches
+    // will complete; one without a verdict counts as having had work).
+    struct HandOver {
+      std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs;
+      std::vector<char>& work;
+      ~HandOver() {
+        for (size_t i = 0; i < evs.size(); ++i)
+          deferred_timing_push(evs[i].first, evs[i].second, i < work.size() ? work[i] != 0 : true);
+      }
+    } hand_over{call_evs, timed_work};
+    if ((uint32_t)cur.large) {   // level 0 from the host's own counts
+      P.p = 0;
+      if (cur.todo) {
+        k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(cur.todo, 8 * sms), 256, 0, s>>>(P);
+        st.kernel_launches += 1;
+      }
+      rc = launch_partition(0, (int)std::min<uint32_t>((uint32_t)(cur.large >> 32), (uint32_t)part_grid_max),
+                            c.opt.test_stall ? 1 : 0);
+      if (rc) return rc;
+      if (timing) timed_work.push_back(1);
+    }
+    if (s1) BQS_CK(cudaEventRecord(ready, s));   // the first lists' runs are written
+    for (int level = 0;; ++level) {
+      if (level > max_levels) return kErrInternal;
+      const int p = level & 1, q = p ^ 1;
+      P.p = p;
+      const uint32_t nlarge = (uint32_t)cur.large;
+      if (nlarge) {
+        st.levels += 1;
+        st.partition_launches += 1;
+        st.active_keys += (int64_t)cur.large_keys;
+      }
+      if (cur.tiny || cur.small || cur.group || cur.big) {
+        // This level's networks (their list lengths are the host's counts).
+        Params Q = P;
+        Q.fixed_counts = 1;
+        Q.n_tiny = cur.tiny;
+        Q.n_small = cur.small;
+        Q.n_group = cur.group;
+        Q.n_big = cur.big;
+        cudaStream_t ns = s1 ? s1 : s;
+        if (s1) BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
+        if (cur.tiny) {
+          k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, ns>>>(Q, p);
+          st.kernel_launches += 1;
+        }
+        if (cur.small || cur.group || cur.big)
+          st.kernel_launches += launch_small<KT, PAIRS>(Q, p, cur.small, cur.group, cur.big, false, ns);
+        st.small_segments += cur.tiny + cur.small + cur.group + cur.big;
+        if (s1) {
+          BQS_CK(cudaEventRecord(done[p], s1));
+          side_work[p] = true;
+        }
+      }
+      // Bookkeeping (and single-block partitioning) write the runs of parity q, which the
+      // networks of the previous level read.
+      if (nlarge || cur.local) {
+        if (side_work[q]) BQS_CK(cudaStreamWaitEvent(s, done[q], 0));
+      }
+      if (nlarge) {
+        k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
+        st.kernel_launches += 1;
+      } else if (cur.local) {
+        // No partition kernel cleared the next level's counts this time.
+        BQS_CK(cudaMemsetAsync(&P.ctrl->lists[q], 0, sizeof(ListCounts), s));
+      }
+      if (cur.local) {
+        st.local_segments += cur.local;
+        launch_local<KT, PAIRS>(P, p, cur.local, s);
+        st.kernel_launches += 1;
+      }
+      BQS_CK(cudaGetLastError());
+      if (!nlarge && !cur.local) break;
+      if (s1) BQS_CK(cudaEventRecord(ready, s));   // the runs of parity q are written
+      BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
+      BQS_CK(cudaEventRecord(counts_ev, s));
+      st.kernel_launches += 1;
+      // Lookahead: the next level's pivot pass and partition.  A segment of the next
+      // level waits for the pivot pass only for a sqrt(n) sample (20000 keys and more,
+      // so only if this level's large segments held that many) or at the depth limit.
+      P.p = q;
+      if (level + 1 >= P.depth_limit || (P.pivot_rule == 1 && cur.large_keys >= 20000)) {
+        k_pivot<KT, PAIRS><<<8 * sms, 256, 0, s>>>(P);
+        st.kernel_launches += 1;
+      }
+      rc = launch_partition(q, part_grid_max, 0);
+      if (rc) return rc;
+      BQS_CK(cudaGetLastError());
+      BQS_CK(cudaEventSynchronize(counts_ev));
+      host_fresh = true;
+      if (host->status) return status_code(host->status);
+      cur = host->lists[q];
+      if (timing) timed_work.push_back((uint32_t)cur.large != 0u);
+      // This level's pivot classes, now that the host knows whether there are any: the
+      // launch (list length as an argument; the next partition has cleared the counts of
+      // parity p, the runs stay until the bookkeeping two levels on) runs after the next
+      // partition instead of before it.
+      const unsigned long long fills = host->lists[p].fill;
+      if ((uint32_t)fills) {
+        Params F = P;
+        F.p = p;
+        F.fixed_counts = 1;
+        F.n_fill = fills;
+        k_fill<KT, PAIRS><<<(int)std::min<unsigned long long>(fills >> 32, 4ull * sms), 256, 0, s>>>(F, p);
+        st.kernel_launches += 1;
+      }
+    }
+    join();
+    if (host_fresh) {
+      st.moved_keys = (int64_t)host->moved_keys;
+      st.equal_keys = (int64_t)host->equal_keys;
+      st.small_keys = (int64_t)host->small_keys;
+      st.local_keys = (int64_t)host->local_keys;
+      st.fallback_pivots = (int64_t)host->fallbacks;
+    } else {
+      st.small_keys = (cur.tiny | cur.small | cur.group | cur.big) ? c.n : 0;
+      st.local_keys = cur.local ? c.n : 0;
+    }
+    st.partition_bytes_per_key = (double)sizeof(U) + (PAIRS ? 4.0 : 0.0);
+    if (timing && !deferred && ev_used) {
+      BQS_CK(cudaEventSynchronize(evs[ev_used - 1].second));
+      double ms = 0;
+      for (size_t i = 0; i < ev_used && i < timed_work.size(); ++i) {
+        if (!timed_work[i]) continue;
+        float t = 0;
+        BQS_CK(cudaEventElapsedTime(&t, evs[i].first, evs[i].second));
+        ms += t;
+      }
+      st.partition_ms = ms;
+    }
+    return kOk;
+  }
   // BQS_OPT_OVERLAP: each level's networks run on a second stream, beside the partition
   // levels (disjoint key ranges).  They read their list lengths from the kernel
   // arguments; `ready` marks the end of the bookkeeping that wrote their runs, `done`

@@ -75,8 +75,14 @@ void prepare_mempool();
 Ctrl* pinned_ctrl(bool* mapped);
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();   // of the current device
 cudaEvent_t counts_event();     // the calling thread's, on the current device (null on failure)
-// The calling thread's second stream and its two events on the current device (null on
-// failure): networks run there beside the partition levels (BQS_OPT_OVERLAP).
+// Deferred partition timing (BQS_OPT_TIMING = 2): an event pair the call may record and
+// hand over with deferred_timing_push (work: the launch had tiles); bqs_timing_collect
+// sums them.
+int deferred_event_pair(cudaEvent_t* e0, cudaEvent_t* e1);
+void deferred_timing_push(cudaEvent_t e0, cudaEvent_t e1, bool work);
+// The calling thread's second stream and its three events (i = 0..2) on the current
+// device (null on failure): networks run there beside the partition levels
+// (BQS_OPT_OVERLAP).
 cudaStream_t side_stream();
 cudaEvent_t side_event(int i);
 

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256) k_fill(Params P, int p) {
   using U = typename KT::U;
   __shared__ uint32_t s_f;
   p = level_parity(P, p);
-  const unsigned long long lc = P.ctrl->lists[p].fill;
+  const unsigned long long lc = P.fixed_counts ? P.n_fill : P.ctrl->lists[p].fill;
   const uint32_t count = min((uint32_t)lc, P.l.cap_fill), tiles = (uint32_t)(lc >> 32);
   const Fill* fills = P.l.fill[p];
   if (count == 0) return;

@@ -434,3 +434,26 @@ def test_networks_on_a_second_stream(bqs, dtype, small_sort, cutoff):
     t = torch.from_numpy(k2).cuda()
     bqs.sort_segmented(t, torch.from_numpy(off).cuda())
     assert_same_bits(t.cpu().numpy(), oracle.sort_segmented(k2, off))
+
+
+def test_deferred_timing_collects_every_partition_launch(bqs):
+    # Timing mode 2: no call waits for its events; bqs_timing_collect sums every
+    # partition launch that had work, once.
+    bqs.set_option("pivot", 1)
+    bqs.collect_timing()
+    bqs.set_option("timing", 2)
+    launches = 0
+    for seed in range(3):
+        a = inputs.make_keys((1 << 22) + seed, "int32", "uniform", seed=seed)
+        got = gpu_sort(bqs, a)
+        st = bqs.stats()
+        assert st["partition_ms"] == 0 and st["partition_launches"] > 0
+        launches += st["partition_launches"]
+        assert_same_bits(got, oracle.sort(a))
+    ms, n = bqs.collect_timing()
+    assert n == launches and ms > 0
+    assert bqs.collect_timing() == (0.0, 0)
+    bqs.set_option("timing", 1)          # the waiting mode reports the same launches
+    a = inputs.make_keys(1 << 22, "int32", "uniform", seed=0)
+    gpu_sort(bqs, a)
+    assert bqs.stats()["partition_ms"] > 0
