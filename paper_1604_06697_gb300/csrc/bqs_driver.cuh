@@ -278,15 +278,31 @@ inline int status_code(int device_status) {
     if (e_ != cudaSuccess) return fail_cuda(e_, #call);           \
   } while (0)
 
-// A non-blocking stream of the calling thread, used only to record the body of the
-// device-side level loop into the conditional node's graph.
-inline cudaStream_t helper_stream() {
-  static thread_local cudaStream_t hs = nullptr;
-  if (!hs && cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    hs = nullptr;
+// Non-blocking streams and events of the calling thread on the current device, used
+// only to record the body of the device-side level loop into the conditional node's
+// graph: the body forks onto the second stream (`fork`) and joins back (`join`).
+struct BodyStreams {
+  cudaStream_t hs = nullptr, hs2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ok = false;
+};
+
+inline BodyStreams& body_streams() {
+  static thread_local BodyStreams per_dev[64];   // streams and events belong to one device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); dev = 0; }
+  BodyStreams& b = per_dev[dev];
+  if (!b.ok) {
+    if ((!b.hs && cudaStreamCreateWithFlags(&b.hs, cudaStreamNonBlocking) != cudaSuccess) ||
+        (!b.hs2 && cudaStreamCreateWithFlags(&b.hs2, cudaStreamNonBlocking) != cudaSuccess) ||
+        (!b.fork && cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!b.join && cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      return b;
+    }
+    b.ok = true;
   }
-  return hs;
+  return b;
 }
 
 // Launches the sorting networks of the `small` list (kWarpSortMax+1 .. group_min keys)
@@ -336,13 +352,19 @@ int launch_small(const Params& P, int p, uint32_t small, uint32_t group, uint32_
 }
 
 // One level of the device-driven loop: every kernel takes the level parity and its work
-// counts from the control block, so the grids are fixed (persistent) sizes.  Optional
-// events bracket the partition launch for BQS_OPT_TIMING.
+// counts from the control block, so the grids are fixed (persistent) sizes.  A level
+// of parity p has two independent parts:
+//  * the partition part -- pivots, partition and children of the lists[p].large
+//    segments (children go to lists[p ^ 1]), their pivot-class fills (lists[p].fill)
+//    and the local partitioning of lists[p].local (leaves go to lists[p ^ 1]);
+//  * the network part -- the segments that the previous level (or the initial split)
+//    put on lists[p]'s tiny / small / group / big lists.
+// They read disjoint lists and write disjoint key ranges, so they may run concurrently.
+// Optional events bracket the partition launch for BQS_OPT_TIMING.
 template <class KT, bool PAIRS>
-void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, bool local_on,
-                        cudaEvent_t e0, cudaEvent_t e1) {
+void enqueue_level_partition(const Params& P, const Variant& var, cudaStream_t s, bool local_on,
+                             cudaEvent_t e0, cudaEvent_t e1) {
   const int sms = sm_count();
-  k_level_begin<<<1, 32, 0, s>>>(P);
   k_pivot<KT, PAIRS><<<8 * sms, 256, 0, s>>>(P);
   if (e0) cudaEventRecord(e0, s);
   var.launch(P, persistent_grid(var.fn, var.threads, var.smem), s);
@@ -350,8 +372,21 @@ void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, boo
   k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P);
   k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
   if (local_on) launch_local<KT, PAIRS>(P, 0, 0, s);
-  k_small_warp<KT, PAIRS><<<16 * sms, 256, 0, s>>>(P, 0);
+}
+
+template <class KT, bool PAIRS>
+void enqueue_level_networks(const Params& P, cudaStream_t s) {
+  k_small_warp<KT, PAIRS><<<16 * sm_count(), 256, 0, s>>>(P, 0);
   launch_small<KT, PAIRS>(P, 0, 0, 0, 0, true, s);
+}
+
+// Both parts in order on one stream.
+template <class KT, bool PAIRS>
+void enqueue_level_body(const Params& P, const Variant& var, cudaStream_t s, bool local_on,
+                        cudaEvent_t e0, cudaEvent_t e1) {
+  k_level_begin<<<1, 32, 0, s>>>(P);
+  enqueue_level_partition<KT, PAIRS>(P, var, s, local_on, e0, e1);
+  enqueue_level_networks<KT, PAIRS>(P, s);
 }
 
 // Pinned flags and events of the calling thread for the device-driven host loop.
@@ -406,10 +441,19 @@ int capture_level_loop(const Params& P, const Variant& var, cudaStream_t s, int 
   cudaGraph_t body = np.conditional.phGraph_out[0];
   BQS_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
 
-  cudaStream_t hs = helper_stream();
-  if (!hs) return kErrCuda;
+  BodyStreams& bs = body_streams();
+  if (!bs.ok) return kErrCuda;
+  cudaStream_t hs = bs.hs;
   BQS_CK(cudaStreamBeginCaptureToGraph(hs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  enqueue_level_body<KT, PAIRS>(P, var, hs, local_on, nullptr, nullptr);
+  // The body forks after k_level_begin: the networks of the previous level's small
+  // segments run on a parallel branch beside this level's partition part.
+  k_level_begin<<<1, 32, 0, hs>>>(P);
+  cudaEventRecord(bs.fork, hs);
+  cudaStreamWaitEvent(bs.hs2, bs.fork, 0);
+  enqueue_level_networks<KT, PAIRS>(P, bs.hs2);
+  cudaEventRecord(bs.join, bs.hs2);
+  enqueue_level_partition<KT, PAIRS>(P, var, hs, local_on, nullptr, nullptr);
+  cudaStreamWaitEvent(hs, bs.join, 0);
   k_level_end<<<1, 32, 0, hs>>>(P, h, max_levels);
   const cudaError_t launch_err = cudaGetLastError();
   cudaGraph_t captured = nullptr;
@@ -659,7 +703,7 @@ int run_call(const Call& c, Stats& st) {
   BQS_CK(cudaStreamIsCapturing(s, &cap));
   const bool device_loop = cap == cudaStreamCaptureStatusActive && !c.fixed_ws;
   if (device_loop && c.partition_only) return kErrUnsupported;   // split is read back
-  if (!device_loop && !c.fixed_ws) helper_stream();   // created outside any capture
+  if (!device_loop && !c.fixed_ws) body_streams();   // created outside any capture
 
   static thread_local Ctrl pageable_ctrl;
   bool host_mapped = false;
