@@ -118,6 +118,9 @@ struct Ctrl {
   // grid-wide barrier of the cooperative single-launch sort
   unsigned int bar_count;           // blocks arrived at the current barrier
   unsigned int bar_gen;             // barriers completed
+  // k_bookkeep with a host copy: blocks finished (the last one copies the block out)
+  unsigned int bk_done;
+  unsigned int bk_pad;
 };
 
 struct Bufs {
@@ -164,6 +167,9 @@ struct Params {
   int fixed_counts;
   uint32_t n_tiny, n_small, n_group, n_big;
   unsigned long long n_fill;   // fill list (count | tiles << 32) for k_fill
+  // Non-null: k_bookkeep's last block copies the control block here (host-mapped
+  // memory), so the host reads a level's counts without a separate copy launch.
+  Ctrl* ctrl_host;
 };
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {

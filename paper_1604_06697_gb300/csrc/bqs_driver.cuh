@@ -887,16 +887,22 @@ int run_call(const Call& c, Stats& st) {
         st.partition_launches += 1;
         st.active_keys += (int64_t)cur.large_keys;
       }
-      if (cur.tiny || cur.small || cur.group || cur.big) {
-        // This level's networks (their list lengths are the host's counts).
+      const bool nets = cur.tiny || cur.small || cur.group || cur.big;
+      // This level's networks: the side stream takes its dependency on the previous
+      // bookkeeping (which wrote their runs) now, and the launches follow the lookahead
+      // partition below, so that the host enqueues the bookkeeping, the work on the
+      // critical path, first.
+      if (nets && s1) BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
+      auto launch_networks = [&]() -> int {
         Params Q = P;
+        Q.p = p;
+        Q.ctrl_host = nullptr;
         Q.fixed_counts = 1;
         Q.n_tiny = cur.tiny;
         Q.n_small = cur.small;
         Q.n_group = cur.group;
         Q.n_big = cur.big;
         cudaStream_t ns = s1 ? s1 : s;
-        if (s1) BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
         if (cur.tiny) {
           k_small_warp<KT, PAIRS><<<(int)std::min<uint32_t>((cur.tiny + 7) / 8, 16 * sms), 256, 0, ns>>>(Q, p);
           st.kernel_launches += 1;
@@ -908,14 +914,21 @@ int run_call(const Call& c, Stats& st) {
           BQS_CK(cudaEventRecord(done[p], s1));
           side_work[p] = true;
         }
-      }
+        BQS_CK(cudaGetLastError());
+        return kOk;
+      };
       // Bookkeeping (and single-block partitioning) write the runs of parity q, which the
       // networks of the previous level read.
       if (nlarge || cur.local) {
         if (side_work[q]) BQS_CK(cudaStreamWaitEvent(s, done[q], 0));
       }
+      // With the control block in host-mapped memory and no single-block partitioning
+      // after it, the bookkeeping's last block copies the counts out itself.
+      const bool bk_copies = nlarge && !cur.local && host_mapped;
       if (nlarge) {
-        k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(P);
+        Params B = P;
+        B.ctrl_host = bk_copies ? host : nullptr;
+        k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(B);
         st.kernel_launches += 1;
       } else if (cur.local) {
         // No partition kernel cleared the next level's counts this time.
@@ -927,11 +940,19 @@ int run_call(const Call& c, Stats& st) {
         st.kernel_launches += 1;
       }
       BQS_CK(cudaGetLastError());
-      if (!nlarge && !cur.local) break;
+      if (!nlarge && !cur.local) {
+        if (nets) {
+          rc = launch_networks();
+          if (rc) return rc;
+        }
+        break;
+      }
       if (s1) BQS_CK(cudaEventRecord(ready, s));   // the runs of parity q are written
-      BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
+      if (!bk_copies) {
+        BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
+        st.kernel_launches += 1;
+      }
       BQS_CK(cudaEventRecord(counts_ev, s));
-      st.kernel_launches += 1;
       // Lookahead: the next level's pivot pass and partition.  A segment of the next
       // level waits for the pivot pass only for a sqrt(n) sample (20000 keys and more,
       // so only if this level's large segments held that many) or at the depth limit.
@@ -943,6 +964,10 @@ int run_call(const Call& c, Stats& st) {
       rc = launch_partition(q, part_grid_max, 0);
       if (rc) return rc;
       BQS_CK(cudaGetLastError());
+      if (nets) {
+        rc = launch_networks();
+        if (rc) return rc;
+      }
       BQS_CK(cudaEventSynchronize(counts_ev));
       host_fresh = true;
       if (host->status) return status_code(host->status);

@@ -565,6 +565,27 @@ __global__ void __launch_bounds__(256) k_bookkeep(Params P) {
       route_warp<KT, PAIRS>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
     }
   }
+  if (P.ctrl_host) {
+    // The last block to finish copies the control block (the next level's counts,
+    // this level's fills, the statistics) to host-mapped memory.
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&P.ctrl->bk_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
+      const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(P.ctrl);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(P.ctrl_host);
+      for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) dst[i] = src[i];
+      __threadfence_system();
+      __syncthreads();
+      if (threadIdx.x == 0) P.ctrl->bk_done = 0;
+    }
+  }
 }
 
 // ---- keys equal to a pivot ----------------------------------------------------------------
