@@ -28,6 +28,10 @@ namespace bqs {
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
   size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0}, big[2] = {0, 0};
+  // A third set of network run lists (tiny, small, group, big) for sorts: the host
+  // level loop rotates three sets, so that a level's bookkeeping never waits for the
+  // networks of the level before it.
+  size_t spare_runs[4] = {0, 0, 0, 0};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -65,6 +69,8 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.local[i] = take((size_t)L.cap_run * sizeof(Run));
     L.fill[i] = take((size_t)L.cap_fill * sizeof(Fill));
   }
+  if (need_alt)
+    for (int k = 0; k < 4; ++k) L.spare_runs[k] = take((size_t)L.cap_run * sizeof(Run));
   L.total = o;
   return L;
 }
@@ -803,20 +809,36 @@ int run_call(const Call& c, Stats& st) {
     // and count read-back, before the host waits for those counts: the device never
     // idles while the host turns around.  Networks (of the lists of parity p, written by
     // the previous bookkeeping) run beside the partitions on a second stream with
-    // BQS_OPT_OVERLAP; `done[p]` marks their end, which the bookkeeping that rewrites the
-    // runs of parity p (two levels on) waits for.
+    // BQS_OPT_OVERLAP.  Their run lists rotate over three sets: level L's networks read
+    // set L mod 3, which the bookkeeping of level L-1 wrote, and level L's bookkeeping
+    // writes set (L+1) mod 3, so it waits only for the networks of level L-2, which
+    // read that set (`done[set]` marks the end of the networks that read a set).
     cudaStream_t s1 = nullptr;
-    cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
+    cudaEvent_t ready = nullptr, done[3] = {nullptr, nullptr, nullptr};
     if (c.opt.overlap) {
       s1 = side_stream();
       ready = side_event(0);
       done[0] = side_event(1);
       done[1] = side_event(2);
-      if (!s1 || !ready || !done[0] || !done[1]) s1 = nullptr;
+      done[2] = side_event(3);
+      if (!s1 || !ready || !done[0] || !done[1] || !done[2]) s1 = nullptr;
     }
-    bool side_work[2] = {false, false};
+    // Set 0 and 1 are the lists of parity 0 and 1 (the first level's runs, written
+    // before the loop, are set 0); set 2 is the layout's spare set.
+    Run* run_sets[3][4] = {{P.l.tiny[0], P.l.small[0], P.l.group[0], P.l.big[0]},
+                           {P.l.tiny[1], P.l.small[1], P.l.group[1], P.l.big[1]},
+                           {(Run*)(w + L.spare_runs[0]), (Run*)(w + L.spare_runs[1]),
+                            (Run*)(w + L.spare_runs[2]), (Run*)(w + L.spare_runs[3])}};
+    auto with_runs = [&](Params X, int parity, int set) {
+      X.l.tiny[parity] = run_sets[set][0];
+      X.l.small[parity] = run_sets[set][1];
+      X.l.group[parity] = run_sets[set][2];
+      X.l.big[parity] = run_sets[set][3];
+      return X;
+    };
+    bool side_work[3] = {false, false, false};
     auto join = [&]() {
-      for (int k = 0; k < 2; ++k)
+      for (int k = 0; k < 3; ++k)
         if (side_work[k]) cudaStreamWaitEvent(s, done[k], 0);
     };
     struct Join {
@@ -893,8 +915,9 @@ int run_call(const Call& c, Stats& st) {
       // partition below, so that the host enqueues the bookkeeping, the work on the
       // critical path, first.
       if (nets && s1) BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
+      const int rset = level % 3, wset = (level + 1) % 3;   // sets read / written
       auto launch_networks = [&]() -> int {
-        Params Q = P;
+        Params Q = with_runs(P, p, rset);
         Q.p = p;
         Q.ctrl_host = nullptr;
         Q.fixed_counts = 1;
@@ -911,22 +934,22 @@ int run_call(const Call& c, Stats& st) {
           st.kernel_launches += launch_small<KT, PAIRS>(Q, p, cur.small, cur.group, cur.big, false, ns);
         st.small_segments += cur.tiny + cur.small + cur.group + cur.big;
         if (s1) {
-          BQS_CK(cudaEventRecord(done[p], s1));
-          side_work[p] = true;
+          BQS_CK(cudaEventRecord(done[rset], s1));
+          side_work[rset] = true;
         }
         BQS_CK(cudaGetLastError());
         return kOk;
       };
-      // Bookkeeping (and single-block partitioning) write the runs of parity q, which the
-      // networks of the previous level read.
+      // Bookkeeping (and single-block partitioning) write the runs of set wset, which the
+      // networks of level L-2 read.
       if (nlarge || cur.local) {
-        if (side_work[q]) BQS_CK(cudaStreamWaitEvent(s, done[q], 0));
+        if (side_work[wset]) BQS_CK(cudaStreamWaitEvent(s, done[wset], 0));
       }
       // With the control block in host-mapped memory and no single-block partitioning
       // after it, the bookkeeping's last block copies the counts out itself.
       const bool bk_copies = nlarge && !cur.local && host_mapped;
       if (nlarge) {
-        Params B = P;
+        Params B = with_runs(P, q, wset);
         B.ctrl_host = bk_copies ? host : nullptr;
         k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((nlarge + 255) / 256, 4 * sms), 256, 0, s>>>(B);
         st.kernel_launches += 1;
@@ -936,7 +959,7 @@ int run_call(const Call& c, Stats& st) {
       }
       if (cur.local) {
         st.local_segments += cur.local;
-        launch_local<KT, PAIRS>(P, p, cur.local, s);
+        launch_local<KT, PAIRS>(with_runs(P, q, wset), p, cur.local, s);
         st.kernel_launches += 1;
       }
       BQS_CK(cudaGetLastError());
