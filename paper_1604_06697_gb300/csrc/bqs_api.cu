@@ -25,7 +25,7 @@ thread_local Ctrl* t_pinned = nullptr;
 // per-thread caches are kept per device.
 constexpr int kMaxDevices = 64;
 thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events[kMaxDevices];
-thread_local cudaEvent_t t_counts_event[kMaxDevices];
+thread_local cudaEvent_t t_counts_event[kMaxDevices][2];
 
 int current_device_slot() {
   int dev = 0;
@@ -99,11 +99,11 @@ void prepare_mempool() {
 Ctrl* pinned_ctrl(bool* mapped) {
   if (!t_pinned) {
     void* p = nullptr;
-    if (cudaMallocHost(&p, sizeof(Ctrl)) != cudaSuccess) {
+    if (cudaMallocHost(&p, 2 * sizeof(Ctrl)) != cudaSuccess) {
       cudaGetLastError();
-      static thread_local Ctrl fallback;  // pageable: copies still complete on sync
+      static thread_local Ctrl fallback[2];  // pageable: copies still complete on sync
       *mapped = false;
-      return &fallback;
+      return fallback;
     }
     t_pinned = (Ctrl*)p;
   }
@@ -116,7 +116,7 @@ std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() {
 }
 
 thread_local cudaStream_t t_side_stream[kMaxDevices];
-thread_local cudaEvent_t t_side_events[kMaxDevices][4];
+thread_local cudaEvent_t t_side_events[kMaxDevices][6];
 
 cudaStream_t side_stream() {
   cudaStream_t& s = t_side_stream[current_device_slot()];
@@ -128,7 +128,7 @@ cudaStream_t side_stream() {
 }
 
 cudaEvent_t side_event(int i) {
-  cudaEvent_t& e = t_side_events[current_device_slot()][i % 4];
+  cudaEvent_t& e = t_side_events[current_device_slot()][i % 6];
   if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     e = nullptr;
@@ -169,8 +169,8 @@ void deferred_timing_push(cudaEvent_t e0, cudaEvent_t e1, bool work) {
   d.work.push_back(work ? 1 : 0);
 }
 
-cudaEvent_t counts_event() {
-  cudaEvent_t& e = t_counts_event[current_device_slot()];
+cudaEvent_t counts_event(int i) {
+  cudaEvent_t& e = t_counts_event[current_device_slot()][i & 1];
   if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     e = nullptr;

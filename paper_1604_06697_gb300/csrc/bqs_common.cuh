@@ -133,6 +133,7 @@ struct Bufs {
 struct Lists {
   Seg* large[2];
   unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
+  uint32_t* tdone[2];             // per large segment: tiles partitioned (fused bookkeeping)
   Run* small[2];
   Run* tiny[2];
   Run* group[2];
@@ -167,7 +168,7 @@ struct Params {
   int fixed_counts;
   uint32_t n_tiny, n_small, n_group, n_big;
   unsigned long long n_fill;   // fill list (count | tiles << 32) for k_fill
-  // Non-null: k_bookkeep's last block copies the control block here (host-mapped
+  // Non-null: the level's last bookkeeping copies the control block here (host-mapped
   // memory), so the host reads a level's counts without a separate copy launch.
   Ctrl* ctrl_host;
 };

@@ -27,6 +27,7 @@ namespace bqs {
 
 struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
+  size_t tdone[2] = {0, 0};
   size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0}, big[2] = {0, 0};
   // A third set of network run lists (tiny, small, group, big) for sorts: the host
   // level loop rotates three sets, so that a level's bookkeeping never waits for the
@@ -61,6 +62,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
   for (int i = 0; i < 2; ++i) {
     L.large[i] = take((size_t)L.cap_large * sizeof(Seg));
     L.cursor[i] = take((size_t)L.cap_large * 8);
+    L.tdone[i] = take((size_t)L.cap_large * sizeof(uint32_t));
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
     L.group[i] = take((size_t)L.cap_run * sizeof(Run));
     L.big[i] = take((size_t)L.cap_run * sizeof(Run));
@@ -115,6 +117,7 @@ struct Variant {
   const void* fn;
   size_t smem;        // dynamic shared memory per block
   void (*launch)(const Params&, int grid, cudaStream_t);
+  void (*launch_fused)(const Params&, int grid, cudaStream_t);   // with the bookkeeping
   cudaError_t (*prepare)();  // allows its shared memory on the current device (before any use)
 };
 
@@ -137,24 +140,29 @@ inline cudaError_t allow_smem_on_device(const void* fn, size_t smem,
   return cudaSuccess;
 }
 
-template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
+template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB, bool FUSED>
 void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
-  k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>
+  k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, FUSED>
       <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, st>>>(P);
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
 cudaError_t prepare_partition_tma() {
-  static std::atomic<unsigned long long> devs{0};
-  return allow_smem_on_device((const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
-                              TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, devs);
+  static std::atomic<unsigned long long> devs{0}, devs_fused{0};
+  const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem;
+  const cudaError_t e = allow_smem_on_device(
+      (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, false>, smem, devs);
+  if (e != cudaSuccess) return e;
+  return allow_smem_on_device((const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, true>,
+                              smem, devs_fused);
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK = 256, int MINB = 1>
 Variant make_tma_variant() {
-  const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>;
+  const void* fn = (const void*)k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, false>;
   const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem;
-  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>,
+  return Variant{T, K, fn, smem, &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, false>,
+                 &launch_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, true>,
                  &prepare_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB>};
 }
 
@@ -670,6 +678,7 @@ int run_call(const Call& c, Stats& st) {
   for (int i = 0; i < 2; ++i) {
     P.l.large[i] = (Seg*)(w + L.large[i]);
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
+    P.l.tdone[i] = (uint32_t*)(w + L.tdone[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
     P.l.group[i] = (Run*)(w + L.group[i]);
     P.l.big[i] = (Run*)(w + L.big[i]);
@@ -813,16 +822,29 @@ int run_call(const Call& c, Stats& st) {
     // set L mod 3, which the bookkeeping of level L-1 wrote, and level L's bookkeeping
     // writes set (L+1) mod 3, so it waits only for the networks of level L-2, which
     // read that set (`done[set]` marks the end of the networks that read a set).
+    // `ready[set]` marks the end of the bookkeeping (and single-block partitioning)
+    // that wrote a set.
+    //
+    // Without single-block partitioning, and with the control block in host-mapped
+    // memory, the loop runs one level deeper: level L+1's bookkeeping is enqueued with
+    // its partition, before the host has read level L's counts.  Its grid is sized for
+    // twice level L's large segments (each has at most two large children; the kernel
+    // reads the exact count on the device), and its last block copies the control block
+    // into the other of two host-mapped blocks, behind the other of two events.
     cudaStream_t s1 = nullptr;
-    cudaEvent_t ready = nullptr, done[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ready[3] = {nullptr, nullptr, nullptr}, done[3] = {nullptr, nullptr, nullptr};
     if (c.opt.overlap) {
       s1 = side_stream();
-      ready = side_event(0);
-      done[0] = side_event(1);
-      done[1] = side_event(2);
-      done[2] = side_event(3);
-      if (!s1 || !ready || !done[0] || !done[1] || !done[2]) s1 = nullptr;
+      for (int k = 0; k < 3; ++k) {
+        ready[k] = side_event(k);
+        done[k] = side_event(3 + k);
+        if (!ready[k] || !done[k]) s1 = nullptr;
+      }
     }
+    const cudaEvent_t counts_ev2 = counts_event(1);
+    const bool deep = local_cutoff <= small_cutoff && host_mapped && counts_ev2 != nullptr;
+    const cudaEvent_t cev[2] = {counts_ev, counts_ev2};
+    Ctrl* const hbuf[2] = {host, host + 1};   // pinned_ctrl: two control blocks
     // Set 0 and 1 are the lists of parity 0 and 1 (the first level's runs, written
     // before the loop, are set 0); set 2 is the layout's spare set.
     Run* run_sets[3][4] = {{P.l.tiny[0], P.l.small[0], P.l.group[0], P.l.big[0]},
@@ -850,7 +872,8 @@ int run_call(const Call& c, Stats& st) {
     // the call for bqs_timing_collect, and the call never waits for them.
     const bool deferred = timing && c.opt.timing == 2;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> call_evs;
-    auto launch_partition = [&](int p, int grid, int stall) -> int {
+    // X: the launch's parameters when they differ from P, with the fused bookkeeping.
+    auto launch_partition = [&](int p, int grid, int stall, const Params* X = nullptr) -> int {
       P.p = p;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (deferred) {
@@ -870,9 +893,10 @@ int run_call(const Call& c, Stats& st) {
         ++ev_used;
         BQS_CK(cudaEventRecord(e0, s));
       }
-      P.test_stall = stall;
-      var.launch(P, grid, s);
-      P.test_stall = 0;
+      Params Y = X ? *X : P;
+      Y.p = p;
+      Y.test_stall = stall;
+      (X ? var.launch_fused : var.launch)(Y, grid, s);
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       st.kernel_launches += 1;
       return kOk;
@@ -887,18 +911,86 @@ int run_call(const Call& c, Stats& st) {
           deferred_timing_push(evs[i].first, evs[i].second, i < work.size() ? work[i] != 0 : true);
       }
     } hand_over{call_evs, timed_work};
+    // Bookkeeping of level lv (writes run set (lv+1) mod 3, waiting for the networks
+    // that read it), sized for `bound` large segments; copy_to: where its last block
+    // copies the control block (null: no copy).
+    auto enqueue_bookkeep = [&](int lv, uint32_t bound, Ctrl* copy_to) -> int {
+      const int bp = lv & 1, ws = (lv + 1) % 3;
+      if (side_work[ws]) BQS_CK(cudaStreamWaitEvent(s, done[ws], 0));
+      Params B = with_runs(P, bp ^ 1, ws);
+      B.p = bp;
+      B.ctrl_host = copy_to;
+      k_bookkeep<KT, PAIRS><<<(int)std::min<uint32_t>((bound + 255) / 256, 4 * sms), 256, 0, s>>>(B);
+      st.kernel_launches += 1;
+      return kOk;
+    };
+    // The deep loop can leave the call with one bookkeeping still to copy into the
+    // thread's host-mapped blocks (the last level's, or after an error): every way out
+    // waits for it, so that the next call does not read a block that is still written.
+    struct LastCopy {
+      cudaEvent_t ev = nullptr;
+      ~LastCopy() {
+        if (ev) cudaEventSynchronize(ev);
+      }
+    } last_copy;
+    // Grids of the lookahead launches for the level after one with counts `lc`: its
+    // segments are the large children of that level's, so at most 2 * lc.large of them,
+    // holding at most lc.large_keys keys in at most large_keys / tile + 2 tiles each.
+    // Both kernels take their work from the device and accept any grid; a small one
+    // spares a deep level the launch of a full persistent grid.  (Without this bound
+    // when the single-block partitioning can add work.)
+    auto next_part_grid = [&](const ListCounts& lc) -> int {
+      if (local_cutoff > small_cutoff) return part_grid_max;
+      const uint64_t t = lc.large_keys / (uint64_t)tile + 4ull * (uint32_t)lc.large + 1;
+      return (int)std::min<uint64_t>(t, (uint64_t)part_grid_max);
+    };
+    auto next_pivot_grid = [&](const ListCounts& lc) -> int {
+      if (local_cutoff > small_cutoff) return 8 * sms;
+      return (int)std::min<uint64_t>(2ull * (uint32_t)lc.large + 1, 8ull * sms);
+    };
+    // Levels of at most two tiles and two segments per partition block (deep loop only)
+    // get the bookkeeping fused into the partition kernel: no bookkeeping launch, and
+    // the counts are copied out by the block that finishes the level's last segment.
+    // The lists a fused level appends to must be empty when it starts: a fused level
+    // leaves its own consumed lists empty, the host clears them after any other level.
+    bool prev_fused = true;   // lists[1] start empty (the control block was zeroed)
+    auto fuse_ok = [&](uint64_t tiles_bound, uint64_t segs_bound) {
+      return deep && tiles_bound <= 2ull * (uint64_t)part_grid_max &&
+             segs_bound <= 2ull * (uint64_t)part_grid_max;
+    };
+    auto enqueue_fused_partition = [&](int lv, int grid, int stall) -> int {
+      const int lp = lv & 1, ws = (lv + 1) % 3;
+      if (!prev_fused) BQS_CK(cudaMemsetAsync(&P.ctrl->lists[lp ^ 1], 0, sizeof(ListCounts), s));
+      if (side_work[ws]) BQS_CK(cudaStreamWaitEvent(s, done[ws], 0));
+      Params X = with_runs(P, lp ^ 1, ws);
+      X.ctrl_host = hbuf[lp];
+      return launch_partition(lp, grid, stall, &X);
+    };
+    if (s1) BQS_CK(cudaEventRecord(ready[0], s));   // the first lists' runs are written
     if ((uint32_t)cur.large) {   // level 0 from the host's own counts
       P.p = 0;
       if (cur.todo) {
         k_pivot<KT, PAIRS><<<(int)std::min<uint32_t>(cur.todo, 8 * sms), 256, 0, s>>>(P);
         st.kernel_launches += 1;
       }
-      rc = launch_partition(0, (int)std::min<uint32_t>((uint32_t)(cur.large >> 32), (uint32_t)part_grid_max),
-                            c.opt.test_stall ? 1 : 0);
+      const uint32_t tiles0 = (uint32_t)(cur.large >> 32);
+      const int grid0 = (int)std::min<uint32_t>(tiles0, (uint32_t)part_grid_max);
+      const int stall0 = c.opt.test_stall ? 1 : 0;
+      const bool fused0 = fuse_ok(tiles0, (uint32_t)cur.large);
+      rc = fused0 ? enqueue_fused_partition(0, grid0, stall0) : launch_partition(0, grid0, stall0);
       if (rc) return rc;
       if (timing) timed_work.push_back(1);
+      prev_fused = fused0;
+      if (deep) {
+        if (!fused0) {
+          rc = enqueue_bookkeep(0, (uint32_t)cur.large, hbuf[0]);
+          if (rc) return rc;
+        }
+        if (s1) BQS_CK(cudaEventRecord(ready[1], s));
+        BQS_CK(cudaEventRecord(cev[0], s));
+        last_copy.ev = cev[0];
+      }
     }
-    if (s1) BQS_CK(cudaEventRecord(ready, s));   // the first lists' runs are written
     for (int level = 0;; ++level) {
       if (level > max_levels) return kErrInternal;
       const int p = level & 1, q = p ^ 1;
@@ -914,8 +1006,8 @@ int run_call(const Call& c, Stats& st) {
       // bookkeeping (which wrote their runs) now, and the launches follow the lookahead
       // partition below, so that the host enqueues the bookkeeping, the work on the
       // critical path, first.
-      if (nets && s1) BQS_CK(cudaStreamWaitEvent(s1, ready, 0));
       const int rset = level % 3, wset = (level + 1) % 3;   // sets read / written
+      if (nets && s1) BQS_CK(cudaStreamWaitEvent(s1, ready[rset], 0));
       auto launch_networks = [&]() -> int {
         Params Q = with_runs(P, p, rset);
         Q.p = p;
@@ -940,6 +1032,59 @@ int run_call(const Call& c, Stats& st) {
         BQS_CK(cudaGetLastError());
         return kOk;
       };
+      if (deep) {
+        // This level's bookkeeping is enqueued; next, level L+1's pivot pass, partition
+        // and bookkeeping, then this level's networks, then the wait for this level's
+        // counts.
+        if (!nlarge) {
+          if (nets) {
+            rc = launch_networks();
+            if (rc) return rc;
+          }
+          break;
+        }
+        P.p = q;
+        if (level + 1 >= P.depth_limit || (P.pivot_rule == 1 && cur.large_keys >= 20000)) {
+          k_pivot<KT, PAIRS><<<next_pivot_grid(cur), 256, 0, s>>>(P);
+          st.kernel_launches += 1;
+        }
+        const uint64_t tiles_next = cur.large_keys / (uint64_t)tile + 4ull * nlarge + 1;
+        if (fuse_ok(tiles_next, 2ull * nlarge)) {
+          rc = enqueue_fused_partition(level + 1, next_part_grid(cur), 0);
+          if (rc) return rc;
+          prev_fused = true;
+        } else {
+          rc = launch_partition(q, next_part_grid(cur), 0);
+          if (rc) return rc;
+          rc = enqueue_bookkeep(level + 1, 2 * nlarge, hbuf[q]);
+          if (rc) return rc;
+          prev_fused = false;
+        }
+        if (s1) BQS_CK(cudaEventRecord(ready[(level + 2) % 3], s));
+        BQS_CK(cudaEventRecord(cev[q], s));
+        last_copy.ev = cev[q];
+        BQS_CK(cudaGetLastError());
+        if (nets) {
+          rc = launch_networks();
+          if (rc) return rc;
+        }
+        BQS_CK(cudaEventSynchronize(cev[p]));
+        host = hbuf[p];
+        host_fresh = true;
+        if (host->status) return status_code(host->status);
+        cur = host->lists[q];
+        if (timing) timed_work.push_back((uint32_t)cur.large != 0u);
+        const unsigned long long fills = host->lists[p].fill;
+        if ((uint32_t)fills) {
+          Params F = P;
+          F.p = p;
+          F.fixed_counts = 1;
+          F.n_fill = fills;
+          k_fill<KT, PAIRS><<<(int)std::min<unsigned long long>(fills >> 32, 4ull * sms), 256, 0, s>>>(F, p);
+          st.kernel_launches += 1;
+        }
+        continue;
+      }
       // Bookkeeping (and single-block partitioning) write the runs of set wset, which the
       // networks of level L-2 read.
       if (nlarge || cur.local) {
@@ -970,7 +1115,7 @@ int run_call(const Call& c, Stats& st) {
         }
         break;
       }
-      if (s1) BQS_CK(cudaEventRecord(ready, s));   // the runs of parity q are written
+      if (s1) BQS_CK(cudaEventRecord(ready[wset], s));   // the runs of set wset are written
       if (!bk_copies) {
         BQS_CK(read_ctrl(P.ctrl, host, host_mapped, s));
         st.kernel_launches += 1;
@@ -981,10 +1126,10 @@ int run_call(const Call& c, Stats& st) {
       // so only if this level's large segments held that many) or at the depth limit.
       P.p = q;
       if (level + 1 >= P.depth_limit || (P.pivot_rule == 1 && cur.large_keys >= 20000)) {
-        k_pivot<KT, PAIRS><<<8 * sms, 256, 0, s>>>(P);
+        k_pivot<KT, PAIRS><<<next_pivot_grid(cur), 256, 0, s>>>(P);
         st.kernel_launches += 1;
       }
-      rc = launch_partition(q, part_grid_max, 0);
+      rc = launch_partition(q, next_part_grid(cur), 0);
       if (rc) return rc;
       BQS_CK(cudaGetLastError());
       if (nets) {

@@ -70,17 +70,19 @@ int dispatch_call(int32_t dtype, const Call& c);   // runs c, keeps its statisti
 int64_t layout_bytes(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff);
 void user_workspace(void** ptr, int64_t* bytes);
 void prepare_mempool();
-// The calling thread's control-block readback buffer: pinned host memory the device
-// can write (mapped = true), or pageable memory if pinning failed.
+// The calling thread's control-block readback buffer, two consecutive control blocks:
+// pinned host memory the device can write (mapped = true), or pageable memory if
+// pinning failed.
 Ctrl* pinned_ctrl(bool* mapped);
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events();   // of the current device
-cudaEvent_t counts_event();     // the calling thread's, on the current device (null on failure)
+// The calling thread's count events i = 0, 1 on the current device (null on failure).
+cudaEvent_t counts_event(int i = 0);
 // Deferred partition timing (BQS_OPT_TIMING = 2): an event pair the call may record and
 // hand over with deferred_timing_push (work: the launch had tiles); bqs_timing_collect
 // sums them.
 int deferred_event_pair(cudaEvent_t* e0, cudaEvent_t* e1);
 void deferred_timing_push(cudaEvent_t e0, cudaEvent_t e1, bool work);
-// The calling thread's second stream and its three events (i = 0..2) on the current
+// The calling thread's second stream and its six events (i = 0..5) on the current
 // device (null on failure): networks run there beside the partition levels
 // (BQS_OPT_OVERLAP).
 cudaStream_t side_stream();

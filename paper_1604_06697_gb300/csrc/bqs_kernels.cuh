@@ -158,51 +158,70 @@ __device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity
   return true;
 }
 
-// Warp-cooperative append of one child segment per lane (`active` lanes with len > 0)
-// to the lists of level q: the sorting network (len <= small_cutoff), the single-block
-// partitioning (len <= local_cutoff) or another partition level.  Every lane of the warp
-// must call it.  Slots come from one atomic per warp and list; a large segment's slot and
-// first tile come from one packed 64-bit atomic, so tile0 grows with the slot index.
-// A large segment's pivot is chosen here when one thread can do it; otherwise the
-// segment is queued on `todo` for k_pivot.
+// Warp-cooperative append of up to two child segments per lane (`act[c]` children with
+// len > 0) to the lists of level q: the sorting network (len <= small_cutoff), the
+// single-block partitioning (len <= local_cutoff) or another partition level.  Every
+// lane of the warp must call it.  Slots come from one atomic per warp and list, for
+// both children at once; a large segment's slot and first tile come from one packed
+// 64-bit atomic, so tile0 grows with the slot index.  A large segment's pivot is chosen
+// here (its sample loads issued before the slot atomic, so that the two latencies
+// overlap) when one thread can do it; otherwise the segment is queued on `todo` for
+// k_pivot.
 template <class KT, bool PAIRS>
-__device__ void route_warp(const Params& P, int q, bool active, int64_t off, int64_t len,
-                           int parity, int depth, bool count_keys = true) {
+__device__ void route_pair(const Params& P, int q, const bool act[2], const int64_t off[2],
+                           const int64_t len[2], int parity, int depth, bool count_keys = true) {
   Ctrl* c = P.ctrl;
   const int lane = threadIdx.x & 31;
   const unsigned below = lanemask_lt();
-  const bool has = active && len > 0;
-  const bool sorted_now = has && len <= P.small_cutoff;
-  const bool tiny = sorted_now && len <= kWarpSortMax;   // one warp per segment
-  const bool big = sorted_now && len > kMaxSmall;        // one larger warp group (key-only)
-  const bool group = sorted_now && !big && len > P.group_min;   // one warp group per segment
-  const bool small = sorted_now && !tiny && !group && !big;     // one warp or block per segment
-  const bool local = has && !sorted_now && len <= P.local_cutoff;
-  const bool large = has && !sorted_now && !local;
+  bool tiny[2], small[2], local[2], group[2], big[2], large[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool has = act[h] && len[h] > 0;
+    const bool sorted_now = has && len[h] <= P.small_cutoff;
+    tiny[h] = sorted_now && len[h] <= kWarpSortMax;        // one warp per segment
+    big[h] = sorted_now && len[h] > kMaxSmall;             // one larger warp group (key-only)
+    group[h] = sorted_now && !big[h] && len[h] > P.group_min;   // one warp group per segment
+    small[h] = sorted_now && !tiny[h] && !group[h] && !big[h];  // one warp or block per segment
+    local[h] = has && !sorted_now && len[h] <= P.local_cutoff;
+    large[h] = has && !sorted_now && !local[h];
+  }
+
+  // Pivots of the large children first: their sample loads overlap the atomics below.
+  uint64_t pkey[2] = {0, 0};
+  uint32_t pval[2] = {0, 0};
+  bool needs_kernel[2] = {false, false};
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (large[h]) needs_kernel[h] = !inline_pivot<KT, PAIRS>(P, off[h], len[h], parity, depth, pkey[h], pval[h]);
 
 #pragma unroll
   for (int kind = 0; kind < 5; ++kind) {
-    const bool mine = kind == 0 ? tiny : kind == 1 ? small : kind == 2 ? local : kind == 3 ? group : big;
-    const unsigned m = __ballot_sync(~0u, mine);
-    if (!m) continue;
-    const int leader = __ffs(m) - 1;
+    bool mine[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      mine[h] = kind == 0 ? tiny[h] : kind == 1 ? small[h] : kind == 2 ? local[h] : kind == 3 ? group[h] : big[h];
+    const unsigned m0 = __ballot_sync(~0u, mine[0]), m1 = __ballot_sync(~0u, mine[1]);
+    if (!(m0 | m1)) continue;
     ListCounts& lc = c->lists[q];
     unsigned int* counter = kind == 0 ? &lc.tiny : kind == 1 ? &lc.small : kind == 2 ? &lc.local
                           : kind == 3 ? &lc.group : &lc.big;
     Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : kind == 2 ? P.l.local[q]
               : kind == 3 ? P.l.group[q] : P.l.big[q];
-    const unsigned keys = __reduce_add_sync(~0u, mine ? (unsigned)len : 0u);  // <= 32 * 2^14
+    const unsigned keys = __reduce_add_sync(~0u, (mine[0] ? (unsigned)len[0] : 0u) +
+                                                     (mine[1] ? (unsigned)len[1] : 0u));  // <= 64 * 2^14
     unsigned int base = 0;
-    if (lane == leader) {
-      base = atomicAdd(counter, (unsigned)__popc(m));
+    if (lane == 0) {
+      base = atomicAdd(counter, (unsigned)(__popc(m0) + __popc(m1)));
       if (count_keys) atomicAdd(kind == 2 ? &c->local_keys : &c->small_keys, (unsigned long long)keys);
     }
-    base = __shfl_sync(~0u, base, leader);
-    if (mine) {
-      const unsigned int slot = base + __popc(m & below);
+    base = __shfl_sync(~0u, base, 0);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!mine[h]) continue;
+      const unsigned int slot = base + (h ? __popc(m0) + __popc(m1 & below) : __popc(m0 & below));
       if (slot < P.l.cap_run) {
         Run r;
-        r.off = off; r.len = len; r.parity = parity; r.pad = depth;   // depth: local runs
+        r.off = off[h]; r.len = len[h]; r.parity = parity; r.pad = depth;   // depth: local runs
         list[slot] = r;
       } else {
         atomicExch(&c->status, kStatusOverflow);
@@ -210,11 +229,15 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
     }
   }
 
-  if (!__any_sync(~0u, large)) return;
-  const unsigned long long tiles = large ? (unsigned long long)tile_count(off, len, P.tile) : 0ull;
-  unsigned long long v = large ? (1ull | (tiles << 32)) : 0ull;
-  unsigned long long keys = large ? (unsigned long long)len : 0ull;
-  const unsigned long long own = v;
+  if (!__any_sync(~0u, large[0] || large[1])) return;
+  unsigned long long own[2], keys = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const unsigned long long tiles = large[h] ? (unsigned long long)tile_count(off[h], len[h], P.tile) : 0ull;
+    own[h] = large[h] ? (1ull | (tiles << 32)) : 0ull;
+    keys += large[h] ? (unsigned long long)len[h] : 0ull;
+  }
+  unsigned long long v = own[0] + own[1];
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
     const unsigned long long x = __shfl_up_sync(~0u, v, o);
@@ -227,29 +250,45 @@ __device__ void route_warp(const Params& P, int q, bool active, int64_t off, int
     atomicAdd(&c->lists[q].large_keys, keys);
   }
   base = __shfl_sync(~0u, base, 31);
-  const unsigned long long old = base + v - own;   // exclusive prefix within the warp
-  const unsigned int slot = (unsigned int)old;
-  bool needs_kernel = false;
-  if (large) {
-    if (slot < P.l.cap_large) {
-      Seg s;
-      s.off = off; s.len = len; s.pkey = 0; s.pval = 0; s.depth = depth; s.parity = parity;
-      s.tile0 = (unsigned int)(old >> 32);
-      needs_kernel = !inline_pivot<KT, PAIRS>(P, off, len, parity, depth, s.pkey, s.pval);
-      P.l.large[q][slot] = s;
-      P.l.cursor[q][slot] = 0ull;
-    } else {
-      atomicExch(&c->status, kStatusOverflow);
+  unsigned long long at = base + v - own[0] - own[1];   // exclusive prefix within the warp
+  unsigned int slot[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    slot[h] = (unsigned int)at;
+    if (large[h]) {
+      if (slot[h] < P.l.cap_large) {
+        Seg sg;
+        sg.off = off[h]; sg.len = len[h]; sg.pkey = pkey[h]; sg.pval = pval[h];
+        sg.depth = depth; sg.parity = parity;
+        sg.tile0 = (unsigned int)(at >> 32);
+        P.l.large[q][slot[h]] = sg;
+        P.l.cursor[q][slot[h]] = 0ull;
+        P.l.tdone[q][slot[h]] = 0u;
+      } else {
+        atomicExch(&c->status, kStatusOverflow);
+        needs_kernel[h] = false;
+      }
     }
+    at += own[h];
   }
-  const unsigned m = __ballot_sync(~0u, needs_kernel);
-  if (m) {
-    const int leader = __ffs(m) - 1;
+  const unsigned k0 = __ballot_sync(~0u, needs_kernel[0]), k1 = __ballot_sync(~0u, needs_kernel[1]);
+  if (k0 | k1) {
     unsigned int tb = 0;
-    if (lane == leader) tb = atomicAdd(&c->lists[q].todo, (unsigned)__popc(m));
-    tb = __shfl_sync(~0u, tb, leader);
-    if (needs_kernel) P.l.todo[q][tb + __popc(m & below)] = slot;
+    if (lane == 0) tb = atomicAdd(&c->lists[q].todo, (unsigned)(__popc(k0) + __popc(k1)));
+    tb = __shfl_sync(~0u, tb, 0);
+    if (needs_kernel[0]) P.l.todo[q][tb + __popc(k0 & below)] = slot[0];
+    if (needs_kernel[1]) P.l.todo[q][tb + __popc(k0) + __popc(k1 & below)] = slot[1];
   }
+}
+
+// One child segment per lane: route_pair with the second child absent.
+template <class KT, bool PAIRS>
+__device__ __forceinline__ void route_warp(const Params& P, int q, bool active, int64_t off,
+                                           int64_t len, int parity, int depth, bool count_keys = true) {
+  const bool act[2] = {active, false};
+  const int64_t o[2] = {off, 0};
+  const int64_t l[2] = {len, 0};
+  route_pair<KT, PAIRS>(P, q, act, o, l, parity, depth, count_keys);
 }
 
 // ---- first work lists --------------------------------------------------------------------
@@ -267,6 +306,7 @@ __global__ void k_init_partition(Params P, int64_t n, uint64_t pkey) {
     s.off = 0; s.len = n; s.pkey = pkey; s.pval = 0; s.depth = 0; s.parity = 0; s.tile0 = 0;
     P.l.large[0][0] = s;
     P.l.cursor[0][0] = 0ull;
+    P.l.tdone[0][0] = 0u;
     P.ctrl->lists[0].large = 1ull | ((unsigned long long)((n - 1) / P.tile + 1) << 32);
     P.ctrl->lists[0].large_keys = (unsigned long long)n;
   }
@@ -497,94 +537,114 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
 
 // ---- children of the partitioned segments ------------------------------------------------
 
+// The bookkeeping of one segment per lane (`active` lanes; every lane of the warp calls
+// it): statistics, the pivot class (written here when short, else queued for k_fill),
+// and both children routed to the lists of level q.
+template <class KT, bool PAIRS>
+__device__ void bookkeep_warp(const Params& P, int p, int q, bool active, unsigned int s) {
+  const int lane = threadIdx.x & 31;
+  Seg sg{};
+  int64_t nlt = 0, ngt = 0, neq = 0;
+  if (active) {
+    sg = P.l.large[p][s];
+    const unsigned long long cur = P.l.cursor[p][s];
+    nlt = (uint32_t)cur;
+    ngt = (uint32_t)(cur >> 32);
+    neq = sg.len - nlt - ngt;
+  }
+  // Statistics, one atomic per warp.
+  unsigned long long moved = (unsigned long long)(nlt + ngt), eq = (unsigned long long)neq;
+  for (int o = 16; o; o >>= 1) {
+    moved += __shfl_xor_sync(~0u, moved, o);
+    eq += __shfl_xor_sync(~0u, eq, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&P.ctrl->moved_keys, moved);
+    atomicAdd(&P.ctrl->equal_keys, eq);
+  }
+  // The keys equal to the pivot are final.  A short run is written here; longer runs
+  // are queued for k_fill (packed atomic).
+  if (active && neq > 0 && neq <= kInlineFill) {
+    using U = typename KT::U;
+    U* fk = (U*)P.b.final_key + sg.off + nlt;
+    for (int64_t j = 0; j < neq; ++j) {
+      fk[j] = (U)sg.pkey;
+      if constexpr (PAIRS) P.b.final_val[sg.off + nlt + j] = sg.pval;
+    }
+  }
+  const bool fills = active && neq > kInlineFill;
+  if (__any_sync(~0u, fills)) {
+    const unsigned long long ftiles = fills ? (unsigned long long)((neq + kFillTile - 1) / kFillTile) : 0ull;
+    unsigned long long v = fills ? (1ull | (ftiles << 32)) : 0ull;
+    const unsigned long long own = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long x = __shfl_up_sync(~0u, v, o);
+      if (lane >= o) v += x;
+    }
+    unsigned long long fb = 0;
+    if (lane == 31) fb = atomicAdd(&P.ctrl->lists[p].fill, v);
+    fb = __shfl_sync(~0u, fb, 31);
+    if (fills) {
+      const unsigned long long old = fb + v - own;
+      const unsigned int slot = (unsigned int)old;
+      if (slot < P.l.cap_fill) {
+        Fill f;
+        f.off = sg.off + nlt; f.len = neq; f.pkey = sg.pkey; f.pval = sg.pval;
+        f.tile0 = (unsigned int)(old >> 32);
+        P.l.fill[p][slot] = f;
+      } else {
+        atomicExch(&P.ctrl->status, kStatusOverflow);
+      }
+    }
+  }
+  if (P.route_children) {   // both sides exclude the pivot class (Sec. 2)
+    const bool act[2] = {active, active};
+    const int64_t off[2] = {sg.off, sg.off + sg.len - ngt};
+    const int64_t len[2] = {nlt, ngt};
+    route_pair<KT, PAIRS>(P, q, act, off, len, sg.parity ^ 1, sg.depth + 1);
+  }
+}
+
+// Copies the control block (the next level's counts, this level's fills, the
+// statistics) to host-mapped memory; every thread of the block calls it.  With
+// clear_p >= 0 the counts of lists[clear_p] (the level's consumed lists) are cleared
+// after the copy, for the next level's bookkeeping.
+__device__ __forceinline__ void copy_ctrl_out(const Params& P, int clear_p) {
+  __threadfence();
+  static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
+  const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(P.ctrl);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(P.ctrl_host);
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    P.ctrl->bk_done = 0;
+    if (clear_p >= 0) clear_counts(&P.ctrl->lists[clear_p]);
+  }
+}
+
 template <class KT, bool PAIRS>
 __global__ void __launch_bounds__(256) k_bookkeep(Params P) {
   const int p = level_parity(P, P.p), q = p ^ 1;
-  const int lane = threadIdx.x & 31;
   const unsigned int count = min((unsigned int)P.ctrl->lists[p].large, P.l.cap_large);
   const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int base = blockIdx.x * blockDim.x; base < count; base += stride) {
-    const unsigned int s = base + threadIdx.x;
-    const bool active = s < count;
-    Seg sg{};
-    int64_t nlt = 0, ngt = 0, neq = 0;
-    if (active) {
-      sg = P.l.large[p][s];
-      const unsigned long long cur = P.l.cursor[p][s];
-      nlt = (uint32_t)cur;
-      ngt = (uint32_t)(cur >> 32);
-      neq = sg.len - nlt - ngt;
-    }
-    // Statistics, one atomic per warp.
-    unsigned long long moved = (unsigned long long)(nlt + ngt), eq = (unsigned long long)neq;
-    for (int o = 16; o; o >>= 1) {
-      moved += __shfl_xor_sync(~0u, moved, o);
-      eq += __shfl_xor_sync(~0u, eq, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&P.ctrl->moved_keys, moved);
-      atomicAdd(&P.ctrl->equal_keys, eq);
-    }
-    // The keys equal to the pivot are final.  A short run is written here; longer runs
-    // are queued for k_fill (packed atomic).
-    if (active && neq > 0 && neq <= kInlineFill) {
-      using U = typename KT::U;
-      U* fk = (U*)P.b.final_key + sg.off + nlt;
-      for (int64_t j = 0; j < neq; ++j) {
-        fk[j] = (U)sg.pkey;
-        if constexpr (PAIRS) P.b.final_val[sg.off + nlt + j] = sg.pval;
-      }
-    }
-    const bool fills = active && neq > kInlineFill;
-    if (__any_sync(~0u, fills)) {
-      const unsigned long long ftiles = fills ? (unsigned long long)((neq + kFillTile - 1) / kFillTile) : 0ull;
-      unsigned long long v = fills ? (1ull | (ftiles << 32)) : 0ull;
-      const unsigned long long own = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long x = __shfl_up_sync(~0u, v, o);
-        if (lane >= o) v += x;
-      }
-      unsigned long long fb = 0;
-      if (lane == 31) fb = atomicAdd(&P.ctrl->lists[p].fill, v);
-      fb = __shfl_sync(~0u, fb, 31);
-      if (fills) {
-        const unsigned long long old = fb + v - own;
-        const unsigned int slot = (unsigned int)old;
-        if (slot < P.l.cap_fill) {
-          Fill f;
-          f.off = sg.off + nlt; f.len = neq; f.pkey = sg.pkey; f.pval = sg.pval;
-          f.tile0 = (unsigned int)(old >> 32);
-          P.l.fill[p][slot] = f;
-        } else {
-          atomicExch(&P.ctrl->status, kStatusOverflow);
-        }
-      }
-    }
-    if (P.route_children) {   // both sides exclude the pivot class (Sec. 2)
-      route_warp<KT, PAIRS>(P, q, active, sg.off, nlt, sg.parity ^ 1, sg.depth + 1);
-      route_warp<KT, PAIRS>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
-    }
-  }
+  for (unsigned int base = blockIdx.x * blockDim.x; base < count; base += stride)
+    bookkeep_warp<KT, PAIRS>(P, p, q, base + threadIdx.x < count, base + threadIdx.x);
   if (P.ctrl_host) {
-    // The last block to finish copies the control block (the next level's counts,
-    // this level's fills, the statistics) to host-mapped memory.
+    // The last block to finish copies the control block out (a single block is last).
     __shared__ bool s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      s_last = atomicAdd(&P.ctrl->bk_done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
-      const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(P.ctrl);
-      unsigned long long* dst = reinterpret_cast<unsigned long long*>(P.ctrl_host);
-      for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) dst[i] = src[i];
-      __threadfence_system();
+    if (gridDim.x > 1) {
       __syncthreads();
-      if (threadIdx.x == 0) P.ctrl->bk_done = 0;
+      if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&P.ctrl->bk_done, 1u) == gridDim.x - 1;
+      }
+      __syncthreads();
+      if (!s_last) return;
+    } else {
+      __syncthreads();
     }
+    copy_ctrl_out(P, -1);
   }
 }
 

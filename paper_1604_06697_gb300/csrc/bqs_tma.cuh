@@ -109,7 +109,10 @@ struct TmaShape {
   static constexpr size_t smem = in_bytes + vin_bytes + out_bytes + vout_bytes + info_bytes;
 };
 
-template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES, int CHUNK_ = 256, int MINB = 1>
+// FUSED: the instantiation for levels of few tiles per block, which also does the
+// bookkeeping of each segment (see the end of the tile loop).
+template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES, int CHUNK_ = 256, int MINB = 1,
+          bool FUSED = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   using U = typename KT::U;
   using S = TmaShape<KT, PAIRS, THREADS, KPT, STAGES, CHUNK_>;
@@ -134,11 +137,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   __shared__ uint32_t s_wcnt[WARPS];
   __shared__ unsigned long long s_base;
   __shared__ int s_abort;
+  __shared__ uint32_t s_done_seg;   // fused bookkeeping: segment whose last tile this was
+  __shared__ int s_copy;            // fused bookkeeping: the level's last segment
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pp = level_parity(P, P.p);
-  // The lists this level's bookkeeping fills (after this kernel) start empty.
-  if (blockIdx.x == 0 && threadIdx.x == 0) clear_counts(&P.ctrl->lists[pp ^ 1]);
+  // The lists this level's bookkeeping fills (after this kernel) start empty.  With the
+  // bookkeeping fused into this kernel the previous level's last bookkeeping (or the
+  // host) has emptied them already: other blocks may append to them at any time.
+  if (!FUSED && blockIdx.x == 0 && threadIdx.x == 0) clear_counts(&P.ctrl->lists[pp ^ 1]);
   const unsigned long long lc = P.ctrl->lists[pp].large;
   const uint32_t nseg = min((uint32_t)lc, P.l.cap_large), ntiles = (uint32_t)(lc >> 32);
   const Seg* __restrict__ segs = P.l.large[pp];
@@ -211,6 +218,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     for (uint32_t i = 0; i < (uint32_t)STAGES && i < count; ++i) issue(i);
 
   uint32_t i = 0;
+  bool aborted = false;   // the whole block left the loop after a wait gave up
   for (; i < count; ++i) {
     const int st = i % STAGES;
     const uint32_t parity = (i / STAGES) & 1;
@@ -281,6 +289,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     // tile's write-out (no thread stages before every thread is past that write-out).
     if (__syncthreads_or(!waited)) {
       if (tid == 0) s_abort = 1;
+      aborted = true;
       break;
     }
     uint32_t off_lt = 0, off_gt = 0, nlt = 0, ngt = 0;
@@ -344,12 +353,45 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     // No barrier here: the next tile's first barrier orders every reuse of s_out, s_wcnt
     // and s_base after this write-out, and the descriptor slot that a lookup at the next
     // tile may refill belongs to a finished chunk.
+    if constexpr (FUSED) {
+      // Fused bookkeeping (levels of few tiles per block): the block that completes a
+      // segment's last tile does the segment's bookkeeping at once, with one warp, and
+      // the block that completes the level's last segment copies the control block out
+      // and empties the level's consumed lists.  Each tile's write-out is published
+      // (block barrier, then a device fence) before the tile counts as done; the
+      // bookkeeping fences before it reads the children's keys and the cursor.
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        const uint32_t nt = (uint32_t)tile_count(ti.off, ti.len, TILE);
+        s_done_seg = atomicAdd(&P.l.tdone[pp][ti.seg], 1u) + 1 == nt ? ti.seg : ~0u;
+      }
+      __syncthreads();
+      const uint32_t ds = s_done_seg;
+      if (ds != ~0u) {
+        if (warp == 0) {
+          __threadfence();
+          bookkeep_warp<KT, PAIRS>(P, pp, pp ^ 1, lane == 0, ds);
+          if (lane == 0) {
+            __threadfence();
+            s_copy = atomicAdd(&P.ctrl->bk_done, 1u) + 1 == nseg;
+          }
+        }
+        __syncthreads();
+        if (s_copy && P.ctrl_host) copy_ctrl_out(P, pp);
+      }
+    }
   }
   if (s_abort && tid == 0) {
     // Let the copies already issued (tiles i .. i+STAGES-1) land before the block's
     // shared memory goes away; each of these waits is bounded too.
     for (uint32_t j = i; j < count && j < i + STAGES; ++j)
       (void)mbar_wait_bounded(&s_bar[j % STAGES], (j / STAGES) & 1, P.ctrl, P.wait_limit);
+  }
+  // With fused bookkeeping a block that gave up copies the control block out itself (its
+  // status word holds the timeout): the level's last segment may never complete.
+  if constexpr (FUSED) {
+    if (P.ctrl_host && aborted) copy_ctrl_out(P, -1);
   }
 }
 
