@@ -116,8 +116,10 @@ struct Variant {
   int threads, kpt;
   const void* fn;
   size_t smem;        // dynamic shared memory per block
-  void (*launch)(const Params&, int grid, cudaStream_t);
-  void (*launch_fused)(const Params&, int grid, cudaStream_t);   // with the bookkeeping
+  // pdl: programmatic dependent launch (the blocks may start while the previous kernel
+  // of the stream finishes; they wait for it before reading anything).
+  void (*launch)(const Params&, int grid, cudaStream_t, bool pdl);
+  void (*launch_fused)(const Params&, int grid, cudaStream_t, bool pdl);   // with the bookkeeping
   cudaError_t (*prepare)();  // allows its shared memory on the current device (before any use)
 };
 
@@ -141,9 +143,23 @@ inline cudaError_t allow_smem_on_device(const void* fn, size_t smem,
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB, bool FUSED>
-void launch_partition_tma(const Params& P, int grid, cudaStream_t st) {
-  k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, FUSED>
-      <<<grid, T, TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem, st>>>(P);
+void launch_partition_tma(const Params& P, int grid, cudaStream_t st, bool pdl) {
+  const size_t smem = TmaShape<KT, PAIRS, T, K, STAGES, CHUNK>::smem;
+  if (!pdl) {
+    k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, FUSED><<<grid, T, smem, st>>>(P);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_partition_tma<KT, PAIRS, T, K, STAGES, CHUNK, MINB, FUSED>, P);
 }
 
 template <class KT, bool PAIRS, int T, int K, int STAGES, int CHUNK, int MINB>
@@ -381,7 +397,7 @@ void enqueue_level_partition(const Params& P, const Variant& var, cudaStream_t s
   const int sms = sm_count();
   k_pivot<KT, PAIRS><<<8 * sms, 256, 0, s>>>(P);
   if (e0) cudaEventRecord(e0, s);
-  var.launch(P, persistent_grid(var.fn, var.threads, var.smem), s);
+  var.launch(P, persistent_grid(var.fn, var.threads, var.smem), s, false);
   if (e1) cudaEventRecord(e1, s);
   k_bookkeep<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P);
   k_fill<KT, PAIRS><<<4 * sms, 256, 0, s>>>(P, 0);
@@ -896,7 +912,7 @@ int run_call(const Call& c, Stats& st) {
       Params Y = X ? *X : P;
       Y.p = p;
       Y.test_stall = stall;
-      (X ? var.launch_fused : var.launch)(Y, grid, s);
+      (X ? var.launch_fused : var.launch)(Y, grid, s, deep);
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       st.kernel_launches += 1;
       return kOk;
@@ -1229,7 +1245,7 @@ int run_call(const Call& c, Stats& st) {
         BQS_CK(cudaEventRecord(e0, s));
       }
       P.test_stall = (level == 0 && c.opt.test_stall) ? 1 : 0;
-      var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s);
+      var.launch(P, (int)std::min<uint32_t>(ntiles, (uint32_t)part_grid_max), s, false);
       P.test_stall = 0;
       if (timing) BQS_CK(cudaEventRecord(e1, s));
       if (side_work) BQS_CK(cudaStreamWaitEvent(s, done, 0));   // the previous level's networks

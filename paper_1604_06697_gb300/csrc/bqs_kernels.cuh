@@ -161,64 +161,112 @@ __device__ bool inline_pivot(const Params& P, int64_t b, int64_t len, int parity
 // Warp-cooperative append of up to two child segments per lane (`act[c]` children with
 // len > 0) to the lists of level q: the sorting network (len <= small_cutoff), the
 // single-block partitioning (len <= local_cutoff) or another partition level.  Every
-// lane of the warp must call it.  Slots come from one atomic per warp and list, for
-// both children at once; a large segment's slot and first tile come from one packed
-// 64-bit atomic, so tile0 grows with the slot index.  A large segment's pivot is chosen
-// here (its sample loads issued before the slot atomic, so that the two latencies
-// overlap) when one thread can do it; otherwise the segment is queued on `todo` for
-// k_pivot.
+// lane of the warp must call it.  The warp reserves its slots with one atomic per list
+// for both children at once, and the atomics of all lists are in flight together
+// (lanes 0..5 take the five run lists and `todo`, lane 31 the packed large-segment
+// atomic, so a large segment's slot and first tile come from one 64-bit atomic and
+// tile0 grows with the slot index).  A large segment's pivot is chosen here, while
+// the atomics are in flight, when one thread can do it; otherwise the segment is
+// queued on `todo` for k_pivot.
 template <class KT, bool PAIRS>
 __device__ void route_pair(const Params& P, int q, const bool act[2], const int64_t off[2],
                            const int64_t len[2], int parity, int depth, bool count_keys = true) {
   Ctrl* c = P.ctrl;
+  ListCounts& lc = c->lists[q];
   const int lane = threadIdx.x & 31;
   const unsigned below = lanemask_lt();
-  bool tiny[2], small[2], local[2], group[2], big[2], large[2];
+  int kind[2];            // 0 tiny, 1 small, 2 local, 3 group, 4 big, 5 large, -1 none
+  bool needs_kernel[2];   // large, with its pivot left to k_pivot
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const bool has = act[h] && len[h] > 0;
     const bool sorted_now = has && len[h] <= P.small_cutoff;
-    tiny[h] = sorted_now && len[h] <= kWarpSortMax;        // one warp per segment
-    big[h] = sorted_now && len[h] > kMaxSmall;             // one larger warp group (key-only)
-    group[h] = sorted_now && !big[h] && len[h] > P.group_min;   // one warp group per segment
-    small[h] = sorted_now && !tiny[h] && !group[h] && !big[h];  // one warp or block per segment
-    local[h] = has && !sorted_now && len[h] <= P.local_cutoff;
-    large[h] = has && !sorted_now && !local[h];
+    const bool tiny = sorted_now && len[h] <= kWarpSortMax;        // one warp per segment
+    const bool big = sorted_now && len[h] > kMaxSmall;             // one larger warp group (key-only)
+    const bool group = sorted_now && !big && len[h] > P.group_min; // one warp group per segment
+    const bool local = has && !sorted_now && len[h] <= P.local_cutoff;
+    kind[h] = !has ? -1 : tiny ? 0 : big ? 4 : group ? 3 : sorted_now ? 1 : local ? 2 : 5;
+    needs_kernel[h] = kind[h] == 5 &&
+                      (depth >= P.depth_limit || (P.pivot_rule == 1 && len[h] >= 20000));
   }
 
-  // Pivots of the large children first: their sample loads overlap the atomics below.
-  uint64_t pkey[2] = {0, 0};
-  uint32_t pval[2] = {0, 0};
-  bool needs_kernel[2] = {false, false};
+  // Per-list masks and counts (uniform over the warp), then the reservations.
+  unsigned m0[5], m1[5], cnt[6];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
-    if (large[h]) needs_kernel[h] = !inline_pivot<KT, PAIRS>(P, off[h], len[h], parity, depth, pkey[h], pval[h]);
+  for (int k = 0; k < 5; ++k) {
+    m0[k] = __ballot_sync(~0u, kind[0] == k);
+    m1[k] = __ballot_sync(~0u, kind[1] == k);
+    cnt[k] = __popc(m0[k]) + __popc(m1[k]);
+  }
+  const unsigned t0 = __ballot_sync(~0u, needs_kernel[0]), t1 = __ballot_sync(~0u, needs_kernel[1]);
+  cnt[5] = __popc(t0) + __popc(t1);
+  unsigned int* ctr = lane == 0 ? &lc.tiny : lane == 1 ? &lc.small : lane == 2 ? &lc.local
+                    : lane == 3 ? &lc.group : lane == 4 ? &lc.big : &lc.todo;
+  unsigned want = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) want = lane == k ? cnt[k] : want;
+  unsigned int rb = 0;
+  if (lane < 6 && want) rb = atomicAdd(ctr, want);
 
+  unsigned long long own[2], lkeys = 0;
 #pragma unroll
-  for (int kind = 0; kind < 5; ++kind) {
-    bool mine[2];
+  for (int h = 0; h < 2; ++h) {
+    const bool large = kind[h] == 5;
+    const unsigned long long tiles = large ? (unsigned long long)tile_count(off[h], len[h], P.tile) : 0ull;
+    own[h] = large ? (1ull | (tiles << 32)) : 0ull;
+    lkeys += large ? (unsigned long long)len[h] : 0ull;
+  }
+  unsigned long long v = own[0] + own[1];
+  const bool any_large = __any_sync(~0u, v != 0ull);
+  unsigned long long lbase = 0;
+  if (any_large) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-      mine[h] = kind == 0 ? tiny[h] : kind == 1 ? small[h] : kind == 2 ? local[h] : kind == 3 ? group[h] : big[h];
-    const unsigned m0 = __ballot_sync(~0u, mine[0]), m1 = __ballot_sync(~0u, mine[1]);
-    if (!(m0 | m1)) continue;
-    ListCounts& lc = c->lists[q];
-    unsigned int* counter = kind == 0 ? &lc.tiny : kind == 1 ? &lc.small : kind == 2 ? &lc.local
-                          : kind == 3 ? &lc.group : &lc.big;
-    Run* list = kind == 0 ? P.l.tiny[q] : kind == 1 ? P.l.small[q] : kind == 2 ? P.l.local[q]
-              : kind == 3 ? P.l.group[q] : P.l.big[q];
-    const unsigned keys = __reduce_add_sync(~0u, (mine[0] ? (unsigned)len[0] : 0u) +
-                                                     (mine[1] ? (unsigned)len[1] : 0u));  // <= 64 * 2^14
-    unsigned int base = 0;
-    if (lane == 0) {
-      base = atomicAdd(counter, (unsigned)(__popc(m0) + __popc(m1)));
-      if (count_keys) atomicAdd(kind == 2 ? &c->local_keys : &c->small_keys, (unsigned long long)keys);
+    for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
+      const unsigned long long x = __shfl_up_sync(~0u, v, o);
+      if (lane >= o) v += x;
+      lkeys += __shfl_xor_sync(~0u, lkeys, o);
     }
-    base = __shfl_sync(~0u, base, 0);
+    if (lane == 31) {
+      lbase = atomicAdd(&lc.large, v);
+      atomicAdd(&lc.large_keys, lkeys);
+    }
+  }
+  if (count_keys) {
+    unsigned sk = 0, lk = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      if (!mine[h]) continue;
-      const unsigned int slot = base + (h ? __popc(m0) + __popc(m1 & below) : __popc(m0 & below));
+      const unsigned l = kind[h] >= 0 && kind[h] <= 4 ? (unsigned)len[h] : 0u;
+      sk += kind[h] == 2 ? 0u : l;
+      lk += kind[h] == 2 ? l : 0u;
+    }
+    sk = __reduce_add_sync(~0u, sk);   // <= 64 * 2^14
+    lk = __reduce_add_sync(~0u, lk);
+    if (lane == 0 && sk) atomicAdd(&c->small_keys, (unsigned long long)sk);
+    if (lane == 1 && lk) atomicAdd(&c->local_keys, (unsigned long long)lk);
+  }
+
+  // Pivots of the large children while the reservations are in flight.
+  uint64_t pkey[2] = {0, 0};
+  uint32_t pval[2] = {0, 0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (kind[h] == 5 && !needs_kernel[h]) {
+      const Elem<KT, PAIRS> piv = rule_pivot<KT, PAIRS>((const typename KT::U*)P.b.key[parity],
+                                                        P.b.val[parity], off[h], len[h], P.pivot_rule);
+      pkey[h] = (uint64_t)KT::unord(piv.k);
+      pval[h] = piv.v;
+    }
+
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (!cnt[k]) continue;
+    const unsigned int base = __shfl_sync(~0u, rb, k);
+    Run* list = k == 0 ? P.l.tiny[q] : k == 1 ? P.l.small[q] : k == 2 ? P.l.local[q]
+              : k == 3 ? P.l.group[q] : P.l.big[q];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (kind[h] != k) continue;
+      const unsigned int slot = base + (h ? __popc(m0[k]) + __popc(m1[k] & below) : __popc(m0[k] & below));
       if (slot < P.l.cap_run) {
         Run r;
         r.off = off[h]; r.len = len[h]; r.parity = parity; r.pad = depth;   // depth: local runs
@@ -229,55 +277,34 @@ __device__ void route_pair(const Params& P, int q, const bool act[2], const int6
     }
   }
 
-  if (!__any_sync(~0u, large[0] || large[1])) return;
-  unsigned long long own[2], keys = 0;
+  if (!any_large) return;
+  lbase = __shfl_sync(~0u, lbase, 31);
+  const unsigned int tb = __shfl_sync(~0u, rb, 5);
+  unsigned long long at = lbase + v - own[0] - own[1];   // exclusive prefix within the warp
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const unsigned long long tiles = large[h] ? (unsigned long long)tile_count(off[h], len[h], P.tile) : 0ull;
-    own[h] = large[h] ? (1ull | (tiles << 32)) : 0ull;
-    keys += large[h] ? (unsigned long long)len[h] : 0ull;
-  }
-  unsigned long long v = own[0] + own[1];
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {          // inclusive scan of the packed (count, tiles)
-    const unsigned long long x = __shfl_up_sync(~0u, v, o);
-    if (lane >= o) v += x;
-    keys += __shfl_xor_sync(~0u, keys, o);
-  }
-  unsigned long long base = 0;
-  if (lane == 31) {
-    base = atomicAdd(&c->lists[q].large, v);
-    atomicAdd(&c->lists[q].large_keys, keys);
-  }
-  base = __shfl_sync(~0u, base, 31);
-  unsigned long long at = base + v - own[0] - own[1];   // exclusive prefix within the warp
-  unsigned int slot[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    slot[h] = (unsigned int)at;
-    if (large[h]) {
-      if (slot[h] < P.l.cap_large) {
+    const unsigned int slot = (unsigned int)at;
+    if (kind[h] == 5) {
+      const bool fits = slot < P.l.cap_large;
+      if (fits) {
         Seg sg;
         sg.off = off[h]; sg.len = len[h]; sg.pkey = pkey[h]; sg.pval = pval[h];
         sg.depth = depth; sg.parity = parity;
         sg.tile0 = (unsigned int)(at >> 32);
-        P.l.large[q][slot[h]] = sg;
-        P.l.cursor[q][slot[h]] = 0ull;
-        P.l.tdone[q][slot[h]] = 0u;
+        P.l.large[q][slot] = sg;
+        P.l.cursor[q][slot] = 0ull;
+        P.l.tdone[q][slot] = 0u;
       } else {
         atomicExch(&c->status, kStatusOverflow);
-        needs_kernel[h] = false;
+      }
+      if (needs_kernel[h]) {
+        // An overflowed segment (the call fails anyway) points k_pivot at slot 0, which
+        // the overflow implies was reserved and written.
+        const unsigned int ts = tb + (h ? __popc(t0) + __popc(t1 & below) : __popc(t0 & below));
+        if (ts < P.l.cap_large) P.l.todo[q][ts] = fits ? slot : 0u;
       }
     }
     at += own[h];
-  }
-  const unsigned k0 = __ballot_sync(~0u, needs_kernel[0]), k1 = __ballot_sync(~0u, needs_kernel[1]);
-  if (k0 | k1) {
-    unsigned int tb = 0;
-    if (lane == 0) tb = atomicAdd(&c->lists[q].todo, (unsigned)(__popc(k0) + __popc(k1)));
-    tb = __shfl_sync(~0u, tb, 0);
-    if (needs_kernel[0]) P.l.todo[q][tb + __popc(k0 & below)] = slot[0];
-    if (needs_kernel[1]) P.l.todo[q][tb + __popc(k0) + __popc(k1 & below)] = slot[1];
   }
 }
 

@@ -140,6 +140,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   __shared__ uint32_t s_done_seg;   // fused bookkeeping: segment whose last tile this was
   __shared__ int s_copy;            // fused bookkeeping: the level's last segment
 
+  // Launched as a programmatic dependent of the stream's previous kernel (deep host
+  // loop), the block may start before that kernel has finished: it waits for it (and
+  // its memory) here, and lets the next level's launch begin.  Both are no-ops
+  // otherwise.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pp = level_parity(P, P.p);
   // The lists this level's bookkeeping fills (after this kernel) start empty.  With the
