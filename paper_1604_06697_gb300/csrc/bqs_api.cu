@@ -116,7 +116,7 @@ std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& timing_events() {
 }
 
 thread_local cudaStream_t t_side_stream[kMaxDevices];
-thread_local cudaEvent_t t_side_events[kMaxDevices][6];
+thread_local cudaEvent_t t_side_events[kMaxDevices][8];
 
 cudaStream_t side_stream() {
   cudaStream_t& s = t_side_stream[current_device_slot()];
@@ -128,7 +128,7 @@ cudaStream_t side_stream() {
 }
 
 cudaEvent_t side_event(int i) {
-  cudaEvent_t& e = t_side_events[current_device_slot()][i % 6];
+  cudaEvent_t& e = t_side_events[current_device_slot()][i % 8];
   if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     e = nullptr;

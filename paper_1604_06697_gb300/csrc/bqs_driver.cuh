@@ -29,10 +29,10 @@ struct Layout {
   size_t alt_key = 0, alt_val = 0, ctrl = 0;
   size_t tdone[2] = {0, 0};
   size_t large[2] = {0, 0}, cursor[2] = {0, 0}, small[2] = {0, 0}, tiny[2] = {0, 0}, todo[2] = {0, 0}, local[2] = {0, 0}, fill[2] = {0, 0}, group[2] = {0, 0}, big[2] = {0, 0};
-  // A third set of network run lists (tiny, small, group, big) for sorts: the host
-  // level loop rotates three sets, so that a level's bookkeeping never waits for the
-  // networks of the level before it.
-  size_t spare_runs[4] = {0, 0, 0, 0};
+  // Two more sets of network run lists (tiny, small, group, big) for sorts: the host
+  // level loop rotates four sets, so that a level's bookkeeping waits only for the
+  // networks of three levels before it.
+  size_t spare_runs[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -72,7 +72,8 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
     L.fill[i] = take((size_t)L.cap_fill * sizeof(Fill));
   }
   if (need_alt)
-    for (int k = 0; k < 4; ++k) L.spare_runs[k] = take((size_t)L.cap_run * sizeof(Run));
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 4; ++k) L.spare_runs[j][k] = take((size_t)L.cap_run * sizeof(Run));
   L.total = o;
   return L;
 }
@@ -834,9 +835,9 @@ int run_call(const Call& c, Stats& st) {
     // and count read-back, before the host waits for those counts: the device never
     // idles while the host turns around.  Networks (of the lists of parity p, written by
     // the previous bookkeeping) run beside the partitions on a second stream with
-    // BQS_OPT_OVERLAP.  Their run lists rotate over three sets: level L's networks read
-    // set L mod 3, which the bookkeeping of level L-1 wrote, and level L's bookkeeping
-    // writes set (L+1) mod 3, so it waits only for the networks of level L-2, which
+    // BQS_OPT_OVERLAP.  Their run lists rotate over four sets: level L's networks read
+    // set L mod 4, which the bookkeeping of level L-1 wrote, and level L's bookkeeping
+    // writes set (L+1) mod 4, so it waits only for the networks of level L-3, which
     // read that set (`done[set]` marks the end of the networks that read a set).
     // `ready[set]` marks the end of the bookkeeping (and single-block partitioning)
     // that wrote a set.
@@ -848,12 +849,13 @@ int run_call(const Call& c, Stats& st) {
     // reads the exact count on the device), and its last block copies the control block
     // into the other of two host-mapped blocks, behind the other of two events.
     cudaStream_t s1 = nullptr;
-    cudaEvent_t ready[3] = {nullptr, nullptr, nullptr}, done[3] = {nullptr, nullptr, nullptr};
+    constexpr int kSets = 4;
+    cudaEvent_t ready[kSets] = {}, done[kSets] = {};
     if (c.opt.overlap) {
       s1 = side_stream();
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kSets; ++k) {
         ready[k] = side_event(k);
-        done[k] = side_event(3 + k);
+        done[k] = side_event(kSets + k);
         if (!ready[k] || !done[k]) s1 = nullptr;
       }
     }
@@ -863,10 +865,12 @@ int run_call(const Call& c, Stats& st) {
     Ctrl* const hbuf[2] = {host, host + 1};   // pinned_ctrl: two control blocks
     // Set 0 and 1 are the lists of parity 0 and 1 (the first level's runs, written
     // before the loop, are set 0); set 2 is the layout's spare set.
-    Run* run_sets[3][4] = {{P.l.tiny[0], P.l.small[0], P.l.group[0], P.l.big[0]},
-                           {P.l.tiny[1], P.l.small[1], P.l.group[1], P.l.big[1]},
-                           {(Run*)(w + L.spare_runs[0]), (Run*)(w + L.spare_runs[1]),
-                            (Run*)(w + L.spare_runs[2]), (Run*)(w + L.spare_runs[3])}};
+    Run* run_sets[kSets][4] = {{P.l.tiny[0], P.l.small[0], P.l.group[0], P.l.big[0]},
+                               {P.l.tiny[1], P.l.small[1], P.l.group[1], P.l.big[1]},
+                               {(Run*)(w + L.spare_runs[0][0]), (Run*)(w + L.spare_runs[0][1]),
+                                (Run*)(w + L.spare_runs[0][2]), (Run*)(w + L.spare_runs[0][3])},
+                               {(Run*)(w + L.spare_runs[1][0]), (Run*)(w + L.spare_runs[1][1]),
+                                (Run*)(w + L.spare_runs[1][2]), (Run*)(w + L.spare_runs[1][3])}};
     auto with_runs = [&](Params X, int parity, int set) {
       X.l.tiny[parity] = run_sets[set][0];
       X.l.small[parity] = run_sets[set][1];
@@ -874,9 +878,9 @@ int run_call(const Call& c, Stats& st) {
       X.l.big[parity] = run_sets[set][3];
       return X;
     };
-    bool side_work[3] = {false, false, false};
+    bool side_work[kSets] = {};
     auto join = [&]() {
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < kSets; ++k)
         if (side_work[k]) cudaStreamWaitEvent(s, done[k], 0);
     };
     struct Join {
@@ -931,7 +935,7 @@ int run_call(const Call& c, Stats& st) {
     // that read it), sized for `bound` large segments; copy_to: where its last block
     // copies the control block (null: no copy).
     auto enqueue_bookkeep = [&](int lv, uint32_t bound, Ctrl* copy_to) -> int {
-      const int bp = lv & 1, ws = (lv + 1) % 3;
+      const int bp = lv & 1, ws = (lv + 1) % kSets;
       if (side_work[ws]) BQS_CK(cudaStreamWaitEvent(s, done[ws], 0));
       Params B = with_runs(P, bp ^ 1, ws);
       B.p = bp;
@@ -975,7 +979,7 @@ int run_call(const Call& c, Stats& st) {
              segs_bound <= 2ull * (uint64_t)part_grid_max;
     };
     auto enqueue_fused_partition = [&](int lv, int grid, int stall) -> int {
-      const int lp = lv & 1, ws = (lv + 1) % 3;
+      const int lp = lv & 1, ws = (lv + 1) % kSets;
       if (!prev_fused) BQS_CK(cudaMemsetAsync(&P.ctrl->lists[lp ^ 1], 0, sizeof(ListCounts), s));
       if (side_work[ws]) BQS_CK(cudaStreamWaitEvent(s, done[ws], 0));
       Params X = with_runs(P, lp ^ 1, ws);
@@ -1022,7 +1026,7 @@ int run_call(const Call& c, Stats& st) {
       // bookkeeping (which wrote their runs) now, and the launches follow the lookahead
       // partition below, so that the host enqueues the bookkeeping, the work on the
       // critical path, first.
-      const int rset = level % 3, wset = (level + 1) % 3;   // sets read / written
+      const int rset = level % kSets, wset = (level + 1) % kSets;   // sets read / written
       if (nets && s1) BQS_CK(cudaStreamWaitEvent(s1, ready[rset], 0));
       auto launch_networks = [&]() -> int {
         Params Q = with_runs(P, p, rset);
@@ -1076,7 +1080,7 @@ int run_call(const Call& c, Stats& st) {
           if (rc) return rc;
           prev_fused = false;
         }
-        if (s1) BQS_CK(cudaEventRecord(ready[(level + 2) % 3], s));
+        if (s1) BQS_CK(cudaEventRecord(ready[(level + 2) % kSets], s));
         BQS_CK(cudaEventRecord(cev[q], s));
         last_copy.ev = cev[q];
         BQS_CK(cudaGetLastError());

@@ -82,7 +82,7 @@ cudaEvent_t counts_event(int i = 0);
 // sums them.
 int deferred_event_pair(cudaEvent_t* e0, cudaEvent_t* e1);
 void deferred_timing_push(cudaEvent_t e0, cudaEvent_t e1, bool work);
-// The calling thread's second stream and its six events (i = 0..5) on the current
+// The calling thread's second stream and its eight events (i = 0..7) on the current
 // device (null on failure): networks run there beside the partition levels
 // (BQS_OPT_OVERLAP).
 cudaStream_t side_stream();

@@ -641,8 +641,9 @@ __device__ __forceinline__ void copy_ctrl_out(const Params& P, int clear_p) {
   static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
   const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(P.ctrl);
   unsigned long long* dst = reinterpret_cast<unsigned long long*>(P.ctrl_host);
+  // No system-scope fence: the host reads the block only after an event behind this
+  // kernel has completed, which orders the kernel's writes before it.
   for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) dst[i] = src[i];
-  __threadfence_system();
   __syncthreads();
   if (threadIdx.x == 0) {
     P.ctrl->bk_done = 0;
