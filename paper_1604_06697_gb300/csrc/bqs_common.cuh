@@ -133,7 +133,7 @@ struct Bufs {
 struct Lists {
   Seg* large[2];
   unsigned long long* cursor[2];  // per large segment: (#< pivot) | (#> pivot) << 32
-  uint32_t* tdone[2];             // per large segment: tiles partitioned (fused bookkeeping)
+  unsigned long long* tdone[2];   // per large segment: finished tiles' counts (fused bookkeeping)
   Run* small[2];
   Run* tiny[2];
   Run* group[2];

@@ -62,7 +62,7 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
   for (int i = 0; i < 2; ++i) {
     L.large[i] = take((size_t)L.cap_large * sizeof(Seg));
     L.cursor[i] = take((size_t)L.cap_large * 8);
-    L.tdone[i] = take((size_t)L.cap_large * sizeof(uint32_t));
+    L.tdone[i] = take((size_t)L.cap_large * sizeof(unsigned long long));
     L.small[i] = take((size_t)L.cap_run * sizeof(Run));
     L.group[i] = take((size_t)L.cap_run * sizeof(Run));
     L.big[i] = take((size_t)L.cap_run * sizeof(Run));
@@ -695,7 +695,7 @@ int run_call(const Call& c, Stats& st) {
   for (int i = 0; i < 2; ++i) {
     P.l.large[i] = (Seg*)(w + L.large[i]);
     P.l.cursor[i] = (unsigned long long*)(w + L.cursor[i]);
-    P.l.tdone[i] = (uint32_t*)(w + L.tdone[i]);
+    P.l.tdone[i] = (unsigned long long*)(w + L.tdone[i]);
     P.l.small[i] = (Run*)(w + L.small[i]);
     P.l.group[i] = (Run*)(w + L.group[i]);
     P.l.big[i] = (Run*)(w + L.big[i]);
@@ -974,9 +974,10 @@ int run_call(const Call& c, Stats& st) {
     // The lists a fused level appends to must be empty when it starts: a fused level
     // leaves its own consumed lists empty, the host clears them after any other level.
     bool prev_fused = true;   // lists[1] start empty (the control block was zeroed)
-    auto fuse_ok = [&](uint64_t tiles_bound, uint64_t segs_bound) {
+    // (Also fewer than kFusedMaxKeys keys: the fields of a segment's completion word.)
+    auto fuse_ok = [&](uint64_t tiles_bound, uint64_t segs_bound, uint64_t keys_bound) {
       return deep && tiles_bound <= 2ull * (uint64_t)part_grid_max &&
-             segs_bound <= 2ull * (uint64_t)part_grid_max;
+             segs_bound <= 2ull * (uint64_t)part_grid_max && keys_bound < kFusedMaxKeys;
     };
     auto enqueue_fused_partition = [&](int lv, int grid, int stall) -> int {
       const int lp = lv & 1, ws = (lv + 1) % kSets;
@@ -996,7 +997,7 @@ int run_call(const Call& c, Stats& st) {
       const uint32_t tiles0 = (uint32_t)(cur.large >> 32);
       const int grid0 = (int)std::min<uint32_t>(tiles0, (uint32_t)part_grid_max);
       const int stall0 = c.opt.test_stall ? 1 : 0;
-      const bool fused0 = fuse_ok(tiles0, (uint32_t)cur.large);
+      const bool fused0 = fuse_ok(tiles0, (uint32_t)cur.large, cur.large_keys);
       rc = fused0 ? enqueue_fused_partition(0, grid0, stall0) : launch_partition(0, grid0, stall0);
       if (rc) return rc;
       if (timing) timed_work.push_back(1);
@@ -1069,7 +1070,7 @@ int run_call(const Call& c, Stats& st) {
           st.kernel_launches += 1;
         }
         const uint64_t tiles_next = cur.large_keys / (uint64_t)tile + 4ull * nlarge + 1;
-        if (fuse_ok(tiles_next, 2ull * nlarge)) {
+        if (fuse_ok(tiles_next, 2ull * nlarge, cur.large_keys)) {
           rc = enqueue_fused_partition(level + 1, next_part_grid(cur), 0);
           if (rc) return rc;
           prev_fused = true;

@@ -293,7 +293,7 @@ __device__ void route_pair(const Params& P, int q, const bool act[2], const int6
         sg.tile0 = (unsigned int)(at >> 32);
         P.l.large[q][slot] = sg;
         P.l.cursor[q][slot] = 0ull;
-        P.l.tdone[q][slot] = 0u;
+        P.l.tdone[q][slot] = 0ull;
       } else {
         atomicExch(&c->status, kStatusOverflow);
       }
@@ -333,7 +333,7 @@ __global__ void k_init_partition(Params P, int64_t n, uint64_t pkey) {
     s.off = 0; s.len = n; s.pkey = pkey; s.pval = 0; s.depth = 0; s.parity = 0; s.tile0 = 0;
     P.l.large[0][0] = s;
     P.l.cursor[0][0] = 0ull;
-    P.l.tdone[0][0] = 0u;
+    P.l.tdone[0][0] = 0ull;
     P.ctrl->lists[0].large = 1ull | ((unsigned long long)((n - 1) / P.tile + 1) << 32);
     P.ctrl->lists[0].large_keys = (unsigned long long)n;
   }
@@ -564,21 +564,16 @@ __global__ void __launch_bounds__(256) k_pivot(Params P) {
 
 // ---- children of the partitioned segments ------------------------------------------------
 
-// The bookkeeping of one segment per lane (`active` lanes; every lane of the warp calls
-// it): statistics, the pivot class (written here when short, else queued for k_fill),
-// and both children routed to the lists of level q.
+// The bookkeeping of one partitioned segment per lane (`active` lanes; every lane of
+// the warp calls it), given the segment and its final counts: statistics, the pivot
+// class (written here when short, else queued for k_fill), and both children routed
+// to the lists of level q.
 template <class KT, bool PAIRS>
-__device__ void bookkeep_warp(const Params& P, int p, int q, bool active, unsigned int s) {
+__device__ void bookkeep_children(const Params& P, int p, int q, bool active, const Seg& sg,
+                                  int64_t nlt, int64_t ngt) {
   const int lane = threadIdx.x & 31;
-  Seg sg{};
-  int64_t nlt = 0, ngt = 0, neq = 0;
-  if (active) {
-    sg = P.l.large[p][s];
-    const unsigned long long cur = P.l.cursor[p][s];
-    nlt = (uint32_t)cur;
-    ngt = (uint32_t)(cur >> 32);
-    neq = sg.len - nlt - ngt;
-  }
+  const int64_t neq = active ? sg.len - nlt - ngt : 0;
+  if (!active) { nlt = 0; ngt = 0; }
   // Statistics, one atomic per warp.
   unsigned long long moved = (unsigned long long)(nlt + ngt), eq = (unsigned long long)neq;
   for (int o = 16; o; o >>= 1) {
@@ -630,6 +625,46 @@ __device__ void bookkeep_warp(const Params& P, int p, int q, bool active, unsign
     const int64_t len[2] = {nlt, ngt};
     route_pair<KT, PAIRS>(P, q, act, off, len, sg.parity ^ 1, sg.depth + 1);
   }
+}
+
+// bookkeep_children for the segment in slot s of the level's list, with the counts
+// the partition tiles accumulated in its cursor.
+template <class KT, bool PAIRS>
+__device__ void bookkeep_warp(const Params& P, int p, int q, bool active, unsigned int s) {
+  Seg sg{};
+  int64_t nlt = 0, ngt = 0;
+  if (active) {
+    sg = P.l.large[p][s];
+    const unsigned long long cur = P.l.cursor[p][s];
+    nlt = (uint32_t)cur;
+    ngt = (uint32_t)(cur >> 32);
+  }
+  bookkeep_children<KT, PAIRS>(P, p, q, active, sg, nlt, ngt);
+}
+
+// Fused bookkeeping (partition kernel, small levels): each finished tile adds
+// (#< | #> << 24 | 1 << 48) of its keys to its segment's word in `tdone`, with one
+// acquire-release atomic; the tile that brings the tile count to the segment's total
+// has the segment's final counts in hand.  The host fuses only levels of fewer than
+// 2^24 keys, so the fields cannot overflow.
+constexpr int kDoneShift = 24;
+__host__ __device__ constexpr unsigned long long done_word(uint32_t nlt, uint32_t ngt) {
+  return (unsigned long long)nlt | ((unsigned long long)ngt << kDoneShift) |
+         (1ull << (2 * kDoneShift));
+}
+constexpr unsigned long long kFusedMaxKeys = 1ull << kDoneShift;
+
+__device__ __forceinline__ unsigned int atomic_add_acq_rel_u32(unsigned int* a, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long atomic_add_acq_rel(unsigned long long* a,
+                                                                 unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(a), "l"(v) : "memory");
+  return old;
 }
 
 // Copies the control block (the next level's counts, this level's fills, the

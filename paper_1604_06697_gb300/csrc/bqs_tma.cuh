@@ -93,7 +93,7 @@ struct TileInfo {
   uint32_t seg;    // index in the level's list (cursor slot)
   uint32_t pval;   // pivot payload
   int32_t parity;  // source buffer
-  int32_t pad;
+  int32_t pad;     // the segment's depth
 };
 
 template <class KT, bool PAIRS, int THREADS, int KPT, int STAGES, int CHUNK_ = 256>
@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   __shared__ unsigned long long s_base;
   __shared__ int s_abort;
   __shared__ uint32_t s_done_seg;   // fused bookkeeping: segment whose last tile this was
+  __shared__ unsigned long long s_done_word;   // ... and its completion word
   __shared__ int s_copy;            // fused bookkeeping: the level's last segment
 
   // Launched as a programmatic dependent of the stream's previous kernel (deep host
@@ -164,22 +165,30 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
   const uint32_t count = t_end - t_begin;
   if (count == 0) return;
 
+  // First tiles of the level's segments in shared memory (the staging buffer, unused
+  // before the first tile) when there are between 8 and kTable of them, so that the
+  // descriptor lookups before the tile loop search there instead of chaining global
+  // loads.
+  constexpr uint32_t kTable = (uint32_t)(S::out_bytes / sizeof(uint32_t));
+  const bool table = nseg >= 8 && nseg <= kTable;
+  const uint32_t* s_t0 = reinterpret_cast<const uint32_t*>(s_out);
+
   // Descriptors of tiles [t_begin + c*CHUNK, +CHUNK) into slot c&1: one binary search
   // per thread, then the segment's fields.
-  auto lookup_chunk = [&](uint32_t c) {
+  auto lookup_chunk = [&](uint32_t c, bool in_table) {
     const uint32_t i = c * CHUNK + tid;
     if (tid < CHUNK && i < count) {
       const uint32_t t = t_begin + i;
       uint32_t lo = 0, hi = nseg;
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (segs[mid].tile0 <= t) lo = mid; else hi = mid;
+        if ((in_table ? s_t0[mid] : segs[mid].tile0) <= t) lo = mid; else hi = mid;
       }
       const Seg sg = segs[lo];
       TileInfo ti;
       ti.off = sg.off; ti.len = sg.len; ti.pkey = sg.pkey; ti.seg = lo; ti.pval = sg.pval;
       ti.parity = sg.parity | (int32_t)((t - sg.tile0) << 1);   // tile index within segment
-      ti.pad = 0;
+      ti.pad = sg.depth;
       s_info[(c & 1) * CHUNK + tid] = ti;
     }
   };
@@ -217,8 +226,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     s_abort = 0;
     fence_mbar_init();
   }
-  lookup_chunk(0);
-  if (count > CHUNK) lookup_chunk(1);
+  if (table) {
+    uint32_t* t0 = reinterpret_cast<uint32_t*>(s_out);
+    for (uint32_t j = tid; j < nseg; j += THREADS) t0[j] = segs[j].tile0;
+    __syncthreads();
+  }
+  lookup_chunk(0, table);
+  if (count > CHUNK) lookup_chunk(1, table);
   __syncthreads();
   if (tid == 0)
     for (uint32_t i = 0; i < (uint32_t)STAGES && i < count; ++i) issue(i);
@@ -231,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     if (i > 0 && i % CHUNK == 0 && (i / CHUNK + 1) * CHUNK < count) {
       // Entering chunk c = i/CHUNK: chunk c-1 is finished, its slot takes chunk c+1
       // (needed once the refills run STAGES tiles ahead into it).
-      lookup_chunk(i / CHUNK + 1);
+      lookup_chunk(i / CHUNK + 1, false);
     }
     // Every thread waits for the tile itself (the mbarrier's acquire makes the bulk copy
     // visible to it); a wait that gave up is acted on at the first block barrier below,
@@ -360,28 +374,33 @@ __global__ void __launch_bounds__(THREADS, MINB) k_partition_tma(Params P) {
     // and s_base after this write-out, and the descriptor slot that a lookup at the next
     // tile may refill belongs to a finished chunk.
     if constexpr (FUSED) {
-      // Fused bookkeeping (levels of few tiles per block): the block that completes a
-      // segment's last tile does the segment's bookkeeping at once, with one warp, and
-      // the block that completes the level's last segment copies the control block out
-      // and empties the level's consumed lists.  Each tile's write-out is published
-      // (block barrier, then a device fence) before the tile counts as done; the
-      // bookkeeping fences before it reads the children's keys and the cursor.
+      // Fused bookkeeping (levels of few tiles per block): every finished tile adds its
+      // counts to its segment's completion word (thread 0, one acquire-release atomic
+      // after a block barrier, which publishes the tile's write-out); the block whose
+      // tile completes the segment does the segment's bookkeeping at once with one
+      // warp, from the tile's descriptor and the word's totals, and the block that
+      // completes the level's last segment copies the control block out and empties the
+      // level's consumed lists.
       __syncthreads();
       if (tid == 0) {
-        __threadfence();
+        const unsigned long long mine = done_word(nlt, ngt);
+        const unsigned long long tot = atomic_add_acq_rel(&P.l.tdone[pp][ti.seg], mine) + mine;
         const uint32_t nt = (uint32_t)tile_count(ti.off, ti.len, TILE);
-        s_done_seg = atomicAdd(&P.l.tdone[pp][ti.seg], 1u) + 1 == nt ? ti.seg : ~0u;
+        s_done_seg = (uint32_t)(tot >> (2 * kDoneShift)) == nt ? ti.seg : ~0u;
+        s_done_word = tot;
       }
       __syncthreads();
-      const uint32_t ds = s_done_seg;
-      if (ds != ~0u) {
+      if (s_done_seg != ~0u) {
         if (warp == 0) {
-          __threadfence();
-          bookkeep_warp<KT, PAIRS>(P, pp, pp ^ 1, lane == 0, ds);
-          if (lane == 0) {
-            __threadfence();
-            s_copy = atomicAdd(&P.ctrl->bk_done, 1u) + 1 == nseg;
-          }
+          constexpr unsigned long long kField = (1ull << kDoneShift) - 1;
+          const unsigned long long tot = s_done_word;
+          Seg sg;
+          sg.off = ti.off; sg.len = ti.len; sg.pkey = ti.pkey; sg.pval = ti.pval;
+          sg.depth = ti.pad; sg.parity = ti.parity & 1; sg.tile0 = 0;
+          bookkeep_children<KT, PAIRS>(P, pp, pp ^ 1, lane == 0, sg, (int64_t)(tot & kField),
+                                       (int64_t)((tot >> kDoneShift) & kField));
+          __syncwarp();
+          if (lane == 0) s_copy = atomic_add_acq_rel_u32(&P.ctrl->bk_done, 1u) + 1 == nseg;
         }
         __syncthreads();
         if (s_copy && P.ctrl_host) copy_ctrl_out(P, pp);

@@ -27,12 +27,15 @@ def bqs():
     return m
 
 
-@pytest.mark.parametrize("level_loop,overlap", [(0, 0), (1, 0), (0, 1)])
-def test_bounded_wait_times_out_and_device_stays_usable(bqs, level_loop, overlap):
+@pytest.mark.parametrize("log2n,level_loop,overlap", [(24, 0, 0), (24, 1, 0), (24, 0, 1), (20, 0, 1)])
+def test_bounded_wait_times_out_and_device_stays_usable(bqs, log2n, level_loop, overlap):
     # level_loop 1: the levels enqueued after the failing one find no work; overlap 1:
-    # the call's stream still waits for the networks on the second stream.
+    # the call's stream still waits for the networks on the second stream.  2^20 keys:
+    # the first level is small enough for the partition kernel with the bookkeeping
+    # fused in, whose failing block copies the control block out itself (the level's
+    # last segment never completes).
     import torch
-    a = inputs.make_keys(1 << 24, "int32", "uniform", seed=8)   # every block owns tiles
+    a = inputs.make_keys(1 << log2n, "int32", "uniform", seed=8)   # every block owns tiles
     t = torch.from_numpy(a).cuda()
     bqs.set_option("level_loop", level_loop)
     bqs.set_option("overlap", overlap)
