@@ -31,18 +31,33 @@ def _check(status: int, where: str) -> None:
         raise BqsError(status, where)
 
 
+_CODE_BY_DTYPE = {}   # torch dtype -> code, filled on first use
+
+
 def _dtype_code(t) -> int:
-    name = str(t.dtype).replace("torch.", "")
-    if name not in DTYPE_CODES:
-        raise TypeError(f"unsupported key dtype {t.dtype}")
-    return DTYPE_CODES[name]
+    code = _CODE_BY_DTYPE.get(t.dtype)
+    if code is None:
+        name = str(t.dtype).replace("torch.", "")
+        if name not in DTYPE_CODES:
+            raise TypeError(f"unsupported key dtype {t.dtype}")
+        code = _CODE_BY_DTYPE[t.dtype] = DTYPE_CODES[name]
+    return code
+
+
+_raw_stream = None   # torch's accessor of the current stream's handle, when it has one
 
 
 def _stream_ptr(t, stream):
+    global _raw_stream
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
+    if _raw_stream is None:
+        import torch
+        _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", False)
+    if _raw_stream:
+        return ctypes.c_void_p(_raw_stream(t.device.index))
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream(t.device)
-    return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
 def _require_cuda(*ts):
