@@ -365,7 +365,12 @@ int bqs_workspace_bytes(int64_t n, int32_t dtype, int32_t with_payload, int64_t 
   if (!bytes || n < 0 || n > kMaxN || nseg < 0 || dtype < BQS_INT32 || dtype > BQS_FLOAT64)
     return BQS_ERR_INVALID;
   const Options o = snapshot_options();
-  const Layout L = plan_layout(n, key_size(dtype), with_payload != 0, nseg, (int)o.small_cutoff, true);
+  // A single array that may take the single-launch path also holds its end-of-launch
+  // lists.
+  const bool single_launch = with_payload == 0 && nseg == 0 && n <= o.coop_max &&
+                             (uint64_t)n < kFusedMaxKeys;
+  const Layout L = plan_layout(n, key_size(dtype), with_payload != 0, nseg, (int)o.small_cutoff, true,
+                               single_launch);
   *bytes = (int64_t)L.total;
   return BQS_OK;
 }

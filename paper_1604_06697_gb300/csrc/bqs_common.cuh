@@ -121,6 +121,10 @@ struct Ctrl {
   // k_bookkeep with a host copy: blocks finished (the last one copies the block out)
   unsigned int bk_done;
   unsigned int bk_pad;
+  // Single-launch sort: the network runs and pivot-class fills of every level, kept
+  // until the end of the launch (`small` counts the runs of all four sizes, `fill`
+  // the fills as count | tiles << 32).
+  ListCounts acc;
 };
 
 struct Bufs {
@@ -171,6 +175,9 @@ struct Params {
   // Non-null: the level's last bookkeeping copies the control block here (host-mapped
   // memory), so the host reads a level's counts without a separate copy launch.
   Ctrl* ctrl_host;
+  // Non-null (single-launch sort): network runs of every size and pivot-class fills
+  // are appended to one list each, counted here, instead of the level's lists.
+  ListCounts* net_acc;
 };
 
 __device__ __forceinline__ void clear_counts(ListCounts* l) {

@@ -6,19 +6,21 @@
 // counts, while the keys (a few MB) sit in L2.  Here one persistent grid (every block
 // resident, cudaLaunchCooperativeKernel) runs every level of the same recursion
 // (Sec. 2, Algorithm 1, breadth first; the block partition step of Sec. 3 per tile)
-// and meets at a grid-wide barrier instead of returning to the host:
+// and meets at one grid-wide barrier per level instead of returning to the host:
 //
-//   level L (lists of parity p, the next level's of parity q = p ^ 1):
+//   level L (large segments of parity p, the next level's of parity q = p ^ 1):
 //     [pivot samples of the segments queued for one, when there are any; barrier]
-//     partition every tile of the large segments, sort the small segments that level
-//     L-1 produced, write the pivot classes that level L-1 found;       barrier
-//     bookkeeping: the children of every partitioned segment go to the lists of q,
-//     pivot classes to q's fill list;                                    barrier
+//     partition every tile of the large segments; the block that completes a
+//     segment's last tile does its bookkeeping at once: large children go to the
+//     lists of q, network runs and pivot-class fills to lists kept for the end of
+//     the launch;                                                         barrier
+//   after the last level: every network run and every fill.
 //
-// Tiles, small segments and fill ranges of one level touch disjoint key ranges, so the
-// first phase needs no order among them.  Every barrier wait is bounded: when one gives
-// up, the block records BQS_ERR_TIMEOUT in the status word and returns (the kernel has
-// no asynchronous copies to wait for), so a failure never hangs the device.
+// Tiles, network runs and fill ranges touch disjoint key ranges, and a small segment's
+// keys stay where its level left them, so the networks can wait for the end.  Every
+// barrier wait is bounded: when one gives up, the block records BQS_ERR_TIMEOUT in the
+// status word and returns (the kernel has no asynchronous copies to wait for), so a
+// failure never hangs the device.
 #pragma once
 
 #include "bqs_small.cuh"
@@ -51,7 +53,9 @@ struct CoopShape {
 // Bounded barrier of all blocks of a cooperative launch, on two words of the control
 // block (cleared by the host before the launch).  The last block to arrive resets the
 // count and advances the generation the others wait on.
-__device__ __forceinline__ bool coop_grid_sync(Ctrl* c, uint32_t limit, int* s_ok) {
+// With clear_p >= 0 the last block to arrive also empties the counts of lists[clear_p]
+// before it releases the others.
+__device__ __forceinline__ bool coop_grid_sync(Ctrl* c, uint32_t limit, int* s_ok, int clear_p = -1) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* gen = &c->bar_gen;
@@ -59,6 +63,7 @@ __device__ __forceinline__ bool coop_grid_sync(Ctrl* c, uint32_t limit, int* s_o
     __threadfence();
     int ok = 1;
     if (atomicAdd(&c->bar_count, 1u) + 1u == gridDim.x) {
+      if (clear_p >= 0) clear_counts(&c->lists[clear_p]);
       atomicExch(&c->bar_count, 0u);
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
@@ -82,11 +87,13 @@ __device__ __forceinline__ bool coop_grid_sync(Ctrl* c, uint32_t limit, int* s_o
 // The block partition step (Sec. 3) on tile t of the level's tile space: the same
 // computation as the TMA-fed kernel (outcome counts in registers, warp scan, one packed
 // atomic per tile, staging in output order, coalesced write-out), with the keys read
-// straight from global memory (L2-resident at these sizes).
+// straight from global memory (L2-resident at these sizes), and the fused bookkeeping
+// of the partition kernel's small-level instantiation.
 template <class KT>
 __device__ __forceinline__ void coop_tile(const Params& P, int p, uint32_t t, uint32_t nseg,
                                           typename KT::U* s_out, uint32_t* s_wcnt,
-                                          unsigned long long* s_base, uint32_t* s_idx) {
+                                          unsigned long long* s_base, uint32_t* s_idx,
+                                          unsigned long long* s_word) {
   using U = typename KT::U;
   using CT = typename Cmp<KT>::T;
   using CS = CoopShape<KT>;
@@ -180,16 +187,33 @@ __device__ __forceinline__ void coop_tile(const Params& P, int p, uint32_t t, ui
   U* dr = dst + sg.off + sg.len - (int64_t)(uint32_t)(base >> 32) - ngt;
   for (uint32_t j = tid; j < nlt; j += T) dl[j] = s_out[j];
   for (uint32_t j = tid; j < ngt; j += T) dr[j] = s_out[nlt + j];
+  // Completion: the tile's write-out is published (block barrier, then thread 0's
+  // acquire-release atomic on the segment's completion word, see done_word); the tile
+  // that completes the segment's count does its bookkeeping with warp 0, from the
+  // segment's descriptor and the word's totals.
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long mine = done_word(nlt, ngt);
+    const unsigned long long tot = atomic_add_acq_rel(&P.l.tdone[p][si], mine) + mine;
+    *s_word = (uint32_t)(tot >> (2 * kDoneShift)) == (uint32_t)tile_count(sg.off, sg.len, TILE) ? tot : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long tot = *s_word;
+  if (tot && warp == 0) {
+    constexpr unsigned long long kField = (1ull << kDoneShift) - 1;
+    bookkeep_children<KT, false>(P, p, p ^ 1, lane == 0, sg, (int64_t)(tot & kField),
+                                 (int64_t)((tot >> kDoneShift) & kField));
+  }
   // The next tile's first barrier (after its segment search) orders the reuse of s_out,
-  // s_wcnt, s_base and s_idx; the caller adds one after its last tile.
+  // s_wcnt, s_base, s_idx and s_word.
 }
 
-// The small segments of the lists of parity p, sorted by the block's warps (segments of
-// at most small_warp_max() keys, one warp each) and warp groups (longer ones; named
-// barriers per group, or the block barrier when a group is the whole block).  Block b
-// takes every gridDim-th entry of each list.
+// The network runs of every level, one list of `count` runs of all sizes, sorted by the
+// block's warps (runs of at most small_warp_max() keys, one warp each) and warp groups
+// (longer ones; named barriers per group, or the block barrier when a group is the
+// whole block), one size class per pass.  Block b takes every gridDim-th run of a pass.
 template <class KT>
-__device__ __forceinline__ void coop_networks(const Params& P, int p, const ListCounts& cur,
+__device__ __forceinline__ void coop_networks(const Params& P, uint32_t count,
                                               typename KT::U* stage) {
   using U = typename KT::U;
   using G = SmallGroup<KT>;
@@ -197,9 +221,10 @@ __device__ __forceinline__ void coop_networks(const Params& P, int p, const List
   constexpr int T = kCoopThreads, W = CS::WARPS;
   constexpr int kMax = small_warp_max<KT, false>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t cap = P.l.cap_run;
-  for (uint32_t s = blockIdx.x * W + warp; s < min(cur.tiny, cap); s += gridDim.x * W) {
-    const Run r = P.l.tiny[p][s];
+  const Run* runs = P.l.small[0];
+  for (uint32_t s = blockIdx.x * W + warp; s < count; s += gridDim.x * W) {
+    const Run r = runs[s];
+    if (r.len > kWarpSortMax) continue;
     U* sx = stage + warp * kWarpSortMax;
     if (r.len <= 32) sort_run<KT, false, 1, 32>(P, r, lane, sx, nullptr, false);
     else if (r.len <= 64) sort_run<KT, false, 2, 32>(P, r, lane, sx, nullptr, false);
@@ -207,8 +232,9 @@ __device__ __forceinline__ void coop_networks(const Params& P, int p, const List
     else sort_run<KT, false, 8, 32>(P, r, lane, sx, nullptr, false);
   }
   __syncthreads();
-  for (uint32_t s = blockIdx.x * W + warp; s < min(cur.small, cap); s += gridDim.x * W) {
-    const Run r = P.l.small[p][s];
+  for (uint32_t s = blockIdx.x * W + warp; s < count; s += gridDim.x * W) {
+    const Run r = runs[s];
+    if (r.len <= kWarpSortMax || r.len > P.group_min) continue;
     U* sw = stage + warp * CS::kWarpStage;
     if (r.len <= 512) group_sort_run<KT, 512 / 32, 32>(P, r, lane, sw);
     else if constexpr (kMax >= 1024) group_sort_run<KT, 1024 / 32, 32>(P, r, lane, sw);
@@ -218,8 +244,9 @@ __device__ __forceinline__ void coop_networks(const Params& P, int p, const List
     constexpr int NG = T / G::T;
     const int g = tid / G::T, gt = tid % G::T;
     U* sw = stage + g * staging_entries<U, G::RMAX, G::T>();
-    for (uint32_t s = blockIdx.x * NG + g; s < min(cur.group, cap); s += gridDim.x * NG) {
-      const Run r = P.l.group[p][s];
+    for (uint32_t s = blockIdx.x * NG + g; s < count; s += gridDim.x * NG) {
+      const Run r = runs[s];
+      if (r.len <= P.group_min || r.len > kMaxSmall) continue;
       const U* src = (const U*)P.b.key[r.parity] + r.off;
       U* dst = (U*)P.b.final_key + r.off;
       if (r.len * 2 <= kMaxSmall)
@@ -233,8 +260,9 @@ __device__ __forceinline__ void coop_networks(const Params& P, int p, const List
     constexpr int NG = T / G::TBIG;
     const int g = tid / G::TBIG, gt = tid % G::TBIG;
     U* sw = stage + g * staging_entries<U, G::RMAX, G::TBIG>();
-    for (uint32_t s = blockIdx.x * NG + g; s < min(cur.big, cap); s += gridDim.x * NG) {
-      const Run r = P.l.big[p][s];
+    for (uint32_t s = blockIdx.x * NG + g; s < count; s += gridDim.x * NG) {
+      const Run r = runs[s];
+      if (r.len <= kMaxSmall) continue;
       group_sort_keys<KT, G::RMAX, G::TBIG, (G::TBIG < T)>((const U*)P.b.key[r.parity] + r.off,
                                                           (U*)P.b.final_key + r.off, (int)r.len, gt, sw);
     }
@@ -269,71 +297,9 @@ __device__ __forceinline__ void coop_fills(const Params& P, int p, unsigned long
   }
 }
 
-// Bookkeeping of the large segments of parity p (the main loop's recursion): the pivot
-// class of each is written now (at most kInlineFill keys) or queued on q's fill list,
-// and both children, pivot class excluded (Sec. 2), go to the lists of q.
-template <class KT>
-__device__ __forceinline__ void coop_bookkeep(const Params& P, int p, int q, uint32_t count) {
-  using U = typename KT::U;
-  const int lane = threadIdx.x & 31;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < count; base += stride) {
-    const uint32_t s = base + threadIdx.x;
-    const bool active = s < count;
-    Seg sg{};
-    int64_t nlt = 0, ngt = 0, neq = 0;
-    if (active) {
-      sg = P.l.large[p][s];
-      const unsigned long long cur = P.l.cursor[p][s];
-      nlt = (uint32_t)cur;
-      ngt = (uint32_t)(cur >> 32);
-      neq = sg.len - nlt - ngt;
-    }
-    unsigned long long moved = (unsigned long long)(nlt + ngt), eq = (unsigned long long)neq;
-    for (int o = 16; o; o >>= 1) {
-      moved += __shfl_xor_sync(~0u, moved, o);
-      eq += __shfl_xor_sync(~0u, eq, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&P.ctrl->moved_keys, moved);
-      atomicAdd(&P.ctrl->equal_keys, eq);
-    }
-    if (active && neq > 0 && neq <= kInlineFill) {
-      U* fk = (U*)P.b.final_key + sg.off + nlt;
-      for (int64_t j = 0; j < neq; ++j) fk[j] = (U)sg.pkey;
-    }
-    const bool fills = active && neq > kInlineFill;
-    if (__any_sync(~0u, fills)) {
-      const unsigned long long ftiles = fills ? (unsigned long long)((neq + kFillTile - 1) / kFillTile) : 0ull;
-      unsigned long long v = fills ? (1ull | (ftiles << 32)) : 0ull;
-      const unsigned long long own = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long x = __shfl_up_sync(~0u, v, o);
-        if (lane >= o) v += x;
-      }
-      unsigned long long fb = 0;
-      if (lane == 31) fb = atomicAdd(&P.ctrl->lists[q].fill, v);
-      fb = __shfl_sync(~0u, fb, 31);
-      if (fills) {
-        const unsigned long long old = fb + v - own;
-        const uint32_t slot = (uint32_t)old;
-        if (slot < P.l.cap_fill) {
-          Fill f;
-          f.off = sg.off + nlt; f.len = neq; f.pkey = sg.pkey; f.pval = 0;
-          f.tile0 = (uint32_t)(old >> 32);
-          P.l.fill[q][slot] = f;
-        } else {
-          atomicExch(&P.ctrl->status, kStatusOverflow);
-        }
-      }
-    }
-    route_warp<KT, false>(P, q, active, sg.off, nlt, sg.parity ^ 1, sg.depth + 1);
-    route_warp<KT, false>(P, q, active, sg.off + sg.len - ngt, ngt, sg.parity ^ 1, sg.depth + 1);
-  }
-}
-
 // The cooperative sort of keys[0, n) (key-only).  Launched with every block resident;
-// the host has cleared the control block.
+// the host has cleared the control block and pointed the network-run and fill lists
+// of both parities at the lists kept for the end (P.net_acc).
 template <class KT>
 __global__ void __launch_bounds__(kCoopThreads, 2) k_coop_sort(Params P, int64_t n, int max_levels) {
   using U = typename KT::U;
@@ -341,7 +307,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_coop_sort(Params P, int64_t
   U* stage = reinterpret_cast<U*>(coop_smem);
   __shared__ PivotSmem<KT, false> psm;
   __shared__ uint32_t s_wcnt[CoopShape<KT>::WARPS];
-  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_base, s_word;
   __shared__ uint32_t s_idx;
   __shared__ int s_ok;
   Ctrl* c = P.ctrl;
@@ -354,44 +320,44 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_coop_sort(Params P, int64_t
   if (!coop_grid_sync(c, P.wait_limit, &s_ok)) return;
   int level = 0;
   for (;; ++level) {
-    const int p = level & 1, q = p ^ 1;
-    // Every block reads the same counts: nothing writes them between the last barrier
-    // and the clear of lists[q] below (a different entry).
+    const int p = level & 1;
+    // Every block reads the same counts: nothing writes lists[p] between the last
+    // barrier and the end of this level's tiles (the bookkeeping appends to lists[q]).
     const volatile ListCounts* vl = &c->lists[p];
-    ListCounts cur;
-    cur.large = vl->large; cur.fill = vl->fill; cur.large_keys = vl->large_keys;
-    cur.small = vl->small; cur.tiny = vl->tiny; cur.todo = vl->todo; cur.local = vl->local;
-    cur.group = vl->group; cur.big = vl->big;
-    const uint32_t nlarge = min((uint32_t)cur.large, P.l.cap_large);
-    const uint32_t ntiles = nlarge ? (uint32_t)(cur.large >> 32) : 0u;
+    const unsigned long long large = vl->large, large_keys = vl->large_keys;
+    const uint32_t todo = vl->todo;
+    const uint32_t nlarge = min((uint32_t)large, P.l.cap_large);
+    const uint32_t ntiles = nlarge ? (uint32_t)(large >> 32) : 0u;
     if (*(volatile int*)&c->status != 0) break;
-    if (!(nlarge | cur.tiny | cur.small | cur.group | cur.big | (uint32_t)cur.fill)) break;
+    if (!nlarge) break;
     if (level > max_levels) {
       if (lead) atomicExch(&c->status, kStatusOverflow);
       break;
     }
-    if (cur.todo && nlarge) {   // sample pivots (sqrt(n) rule) and depth-limit fallbacks
+    if (todo) {   // sample pivots (sqrt(n) rule) and depth-limit fallbacks
       pivot_pass<KT, false>(P, p, psm);
       if (!coop_grid_sync(c, P.wait_limit, &s_ok)) return;
     }
-    if (lead) clear_counts(&c->lists[q]);   // last read by the previous bookkeeping
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-      coop_tile<KT>(P, p, t, nlarge, stage, s_wcnt, &s_base, &s_idx);
-    __syncthreads();   // the tiles' staging area becomes the networks'
-    coop_networks<KT>(P, p, cur, stage);
-    coop_fills<KT>(P, p, cur.fill, &s_idx);
-    if (!coop_grid_sync(c, P.wait_limit, &s_ok)) return;
-    coop_bookkeep<KT>(P, p, q, nlarge);
+      coop_tile<KT>(P, p, t, nlarge, stage, s_wcnt, &s_base, &s_idx, &s_word);
     if (lead) {
-      if (nlarge) {
-        c->levels_run += 1;
-        c->active_total += cur.large_keys;
-      }
-      c->small_runs += cur.tiny + cur.small + cur.group + cur.big;
+      c->levels_run += 1;
+      c->active_total += large_keys;
     }
-    if (!coop_grid_sync(c, P.wait_limit, &s_ok)) return;
+    // The last block to arrive empties lists[p]: the next level's bookkeeping appends
+    // to them.
+    if (!coop_grid_sync(c, P.wait_limit, &s_ok, p)) return;
   }
-  if (lead) c->level = level;
+  // Every level's network runs and pivot-class fills.
+  const volatile ListCounts* acc = P.net_acc;
+  const uint32_t nruns = min(acc->small, P.l.cap_run);
+  const unsigned long long fills = acc->fill;
+  coop_networks<KT>(P, nruns, stage);
+  coop_fills<KT>(P, 0, fills, &s_idx);
+  if (lead) {
+    c->level = level;
+    c->small_runs = nruns;
+  }
 }
 
 }  // namespace bqs

@@ -33,6 +33,9 @@ struct Layout {
   // level loop rotates four sets, so that a level's bookkeeping waits only for the
   // networks of three levels before it.
   size_t spare_runs[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  // Single-launch sort: the network runs and pivot-class fills of every level.
+  size_t acc_runs = 0, acc_fill = 0;
+  uint32_t cap_acc_runs = 0, cap_acc_fill = 0;
   size_t total = 0;
   uint32_t cap_large = 0, cap_run = 0, cap_fill = 0;
 };
@@ -44,7 +47,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // level, one entry per caller segment).  Sized for C <= kMaxSmall, which holds for every
 // sort that the cutoff applies to (key-value sorts clamp C to kMaxSmall).
 inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int small_cutoff,
-                          bool need_alt) {
+                          bool need_alt, bool single_launch = false) {
   Layout L;
   small_cutoff = std::min(small_cutoff, kMaxSmall);
   const uint64_t cap_large = (uint64_t)n / (uint64_t)(small_cutoff + 1) + 2;
@@ -74,6 +77,21 @@ inline Layout plan_layout(int64_t n, int key_size, bool pairs, int64_t nseg, int
   if (need_alt)
     for (int j = 0; j < 2; ++j)
       for (int k = 0; k < 4; ++k) L.spare_runs[j][k] = take((size_t)L.cap_run * sizeof(Run));
+  if (single_launch) {
+    // Every level appends at most two runs and one fill per large segment, at most
+    // cap_large of them per level, over at most 2 log2 n + 3 + 8 key_size + 40 levels
+    // (the default depth limit and one halving per key bit); never more runs or fills
+    // than keys.  Past this the launch reports an overflow.
+    int lg = 0;
+    for (int64_t t = n; t > 1; t >>= 1) ++lg;
+    const uint64_t levels = 2ull * (uint64_t)lg + 3 + 8ull * (uint64_t)key_size + 40;
+    L.cap_acc_runs = (uint32_t)std::min<uint64_t>(std::min<uint64_t>((uint64_t)n, 2 * levels * cap_large) + 2,
+                                                  0xFFFFFFF0ull);
+    L.cap_acc_fill = (uint32_t)std::min<uint64_t>(std::min<uint64_t>((uint64_t)n, levels * cap_large) + 2,
+                                                  0xFFFFFFF0ull);
+    L.acc_runs = take((size_t)L.cap_acc_runs * sizeof(Run));
+    L.acc_fill = take((size_t)L.cap_acc_fill * sizeof(Fill));
+  }
   L.total = o;
   return L;
 }
@@ -561,7 +579,7 @@ int run_levels_ahead(Params P, const Variant& var, cudaStream_t s, int max_level
   st.levels = (int64_t)host->levels_run;
   st.active_keys = (int64_t)host->active_total;
   st.local_segments = (int64_t)host->local_runs;
-  st.small_segments = (int64_t)host->small_runs;
+  st.small_segments = (int64_t)host->acc.small;
   st.moved_keys = (int64_t)host->moved_keys;
   st.equal_keys = (int64_t)host->equal_keys;
   st.small_keys = (int64_t)host->small_keys;
@@ -588,7 +606,8 @@ constexpr int kCoopRefused = 1;
 
 template <class KT>
 int run_coop(Params P, int64_t n, int max_levels, bool timing, int test_stall, cudaStream_t s,
-             Ctrl* host, bool host_mapped, Stats& st) {
+             Ctrl* host, bool host_mapped, Stats& st, Run* acc_runs, uint32_t cap_acc_runs,
+             Fill* acc_fill, uint32_t cap_acc_fill) {
   const void* fn = (const void*)k_coop_sort<KT>;
   const int grid = persistent_grid(fn, kCoopThreads, CoopShape<KT>::smem);
   int coop = 0, dev = 0;
@@ -599,6 +618,15 @@ int run_coop(Params P, int64_t n, int max_levels, bool timing, int test_stall, c
   }
   P.local_cutoff = P.small_cutoff;   // no single-block local partitioning here
   P.tile = CoopShape<KT>::TILE;      // the tile space of this kernel's partition step
+  // Network runs of every size and pivot-class fills go to one list each, kept for the
+  // end of the launch.
+  P.net_acc = &P.ctrl->acc;
+  for (int i = 0; i < 2; ++i) {
+    P.l.tiny[i] = P.l.small[i] = P.l.group[i] = P.l.big[i] = acc_runs;
+    P.l.fill[i] = acc_fill;
+  }
+  P.l.cap_run = cap_acc_runs;
+  P.l.cap_fill = cap_acc_fill;
   P.test_stall = test_stall;
   P.device_loop = 0;
   void* args[] = {(void*)&P, (void*)&n, (void*)&max_levels};
@@ -633,7 +661,7 @@ int run_coop(Params P, int64_t n, int max_levels, bool timing, int test_stall, c
   st.moved_keys = (int64_t)host->moved_keys;
   st.equal_keys = (int64_t)host->equal_keys;
   st.small_keys = (int64_t)host->small_keys;
-  st.small_segments = (int64_t)host->small_runs;
+  st.small_segments = (int64_t)host->acc.small;
   st.fallback_pivots = (int64_t)host->fallbacks;
   st.partition_bytes_per_key = (double)sizeof(typename KT::U);
   if (timing) {
@@ -670,7 +698,14 @@ int run_call(const Call& c, Stats& st) {
                                        ? kLocalL
                                        : (int)std::min<int64_t>(c.opt.local_cutoff, kLocalL));
 
-  const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only);
+  // Single arrays of up to BQS_OPT_COOP_MAX keys (fewer than kFusedMaxKeys) may run
+  // every level in one launch.
+  const bool single_launch = !PAIRS && !c.fixed_ws && !c.partition_only && !c.seg_offsets &&
+                             c.opt.level_loop == 0 && c.opt.small_sort == 0 &&
+                             local_cutoff <= small_cutoff && c.n > small_cutoff &&
+                             c.n <= c.opt.coop_max && (uint64_t)c.n < kFusedMaxKeys;
+  const Layout L = plan_layout(c.n, (int)sizeof(U), PAIRS, c.nseg, small_cutoff, !c.partition_only,
+                               single_launch);
   Scratch scratch;
   int rc = kOk;
   if (c.fixed_ws) {   // allocation-free call: the caller's fixed scratch must be enough
@@ -745,11 +780,11 @@ int run_call(const Call& c, Stats& st) {
 
   if constexpr (!PAIRS) {
     // Single arrays of up to BQS_OPT_COOP_MAX keys: every level in one launch.
-    if (!device_loop && !c.fixed_ws && !c.partition_only && !c.seg_offsets &&
-        c.opt.level_loop == 0 && c.opt.small_sort == 0 && local_cutoff <= small_cutoff &&
-        c.n > small_cutoff && c.n <= c.opt.coop_max) {
+    if (!device_loop && single_launch) {
       const int rc_coop = run_coop<KT>(P, c.n, P.depth_limit + 8 * (int)sizeof(U) + 40, timing,
-                                       c.opt.test_stall ? 1 : 0, s, host, host_mapped, st);
+                                       c.opt.test_stall ? 1 : 0, s, host, host_mapped, st,
+                                       (Run*)(w + L.acc_runs), L.cap_acc_runs,
+                                       (Fill*)(w + L.acc_fill), L.cap_acc_fill);
       if (rc_coop != kCoopRefused) return rc_coop;
     }
   }

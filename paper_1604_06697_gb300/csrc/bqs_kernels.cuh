@@ -200,8 +200,11 @@ __device__ void route_pair(const Params& P, int q, const bool act[2], const int6
   }
   const unsigned t0 = __ballot_sync(~0u, needs_kernel[0]), t1 = __ballot_sync(~0u, needs_kernel[1]);
   cnt[5] = __popc(t0) + __popc(t1);
-  unsigned int* ctr = lane == 0 ? &lc.tiny : lane == 1 ? &lc.small : lane == 2 ? &lc.local
-                    : lane == 3 ? &lc.group : lane == 4 ? &lc.big : &lc.todo;
+  // (With net_acc the four network sizes share one list and one counter.)
+  unsigned int* const netc = P.net_acc ? &P.net_acc->small : nullptr;
+  unsigned int* ctr = lane == 0 ? (netc ? netc : &lc.tiny) : lane == 1 ? (netc ? netc : &lc.small)
+                    : lane == 2 ? &lc.local : lane == 3 ? (netc ? netc : &lc.group)
+                    : lane == 4 ? (netc ? netc : &lc.big) : &lc.todo;
   unsigned want = 0;
 #pragma unroll
   for (int k = 0; k < 6; ++k) want = lane == k ? cnt[k] : want;
@@ -604,7 +607,7 @@ __device__ void bookkeep_children(const Params& P, int p, int q, bool active, co
       if (lane >= o) v += x;
     }
     unsigned long long fb = 0;
-    if (lane == 31) fb = atomicAdd(&P.ctrl->lists[p].fill, v);
+    if (lane == 31) fb = atomicAdd(P.net_acc ? &P.net_acc->fill : &P.ctrl->lists[p].fill, v);
     fb = __shfl_sync(~0u, fb, 31);
     if (fills) {
       const unsigned long long old = fb + v - own;
