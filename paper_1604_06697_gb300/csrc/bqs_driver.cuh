@@ -957,7 +957,7 @@ int run_call(const Call& c, Stats& st) {
       return kOk;
     };
     // Every way out of the call hands the deferred pairs over (their recorded launches
-    // will complete; one without a verdict counts as having had work).
+    // will complete; one whose outcome is unknown counts as having had work).
     struct HandOver {
       std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs;
       std::vector<char>& work;
