@@ -249,14 +249,16 @@ typedef enum {
                                slower: the block's load, partition and network phases
                                run one after another at 2 blocks per SM) */
   BQS_OPT_COOP_MAX = 12     /* single-array key-only sorts (bqs_sort) of more than the
-                               small cutoff and at most this many keys run every level in
-                               one cooperative launch (all blocks resident, bounded grid-
-                               wide barriers between the phases of a level) instead of the
+                               small cutoff and at most this many keys (and fewer than
+                               2^24) run every level in one cooperative launch (all
+                               blocks resident, one bounded grid-wide barrier per level,
+                               the networks after the last level) instead of the
                                host-driven level loop; the call then reads the control
-                               block back once, at its end.  0 = never (the default: at
-                               2^18..2^22 keys it measured no faster than the host loop,
-                               its grid-wide barriers waiting on the slowest block).
-                               Not used on a stream that is being captured, by
+                               block back once, at its end, and its scratch holds the
+                               network runs and fills of every level.  0 = never (the
+                               default; the autotuner offers it up to 2^22 keys, and at
+                               2^20 keys it is faster than the host loop, at 2^22
+                               slower).  Not used on a stream that is being captured, by
                                bqs_sort_noalloc, with BQS_OPT_LEVEL_LOOP = 1,
                                BQS_OPT_SMALL_SORT = 1 or local partitioning on, or when
                                the device refuses the cooperative launch (the host loop
